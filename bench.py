@@ -1,0 +1,340 @@
+#!/usr/bin/env python
+"""PnP-ADMM reconstruction throughput on GB300 (voxel-iterations per second).
+
+Workload (one "step"): the 512 x 512 x 16 drifting-blob volume behind one
+coded measurement (Bernoulli(0.3) DMD patterns, Poisson peak 50 + Gaussian
+sigma 0.02), reconstructed by 100 iterations of Algorithm 1 with the TV prior
+and the z-smoothness Gauss-Seidel sweep (rho = 1, lambda = 0.05, gamma = 0.2,
+20 Chambolle steps per prox).  A step re-packs the DMD patterns and runs the
+whole solve through the C ABI.  Inputs are seeded synthetic data.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun, one independent measurement per rank (weak
+scaling, no data-path collective).  --impl reference times the FP64 CPU
+oracle on the same workload (bounded sample per step) on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "tvz_512x512x16"
+PARAMS = dict(rho=1.0, lam=0.05, gamma=0.2, iters=100, denoiser="tv", tv_inner=20,
+              tv_tau=0.125)
+METRIC = "PnP-ADMM voxel-iterations/s"
+UNIT = "voxel-it/s"
+L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
+DOMINANT = "tv_tile"
+TIMING_PERIOD = 16  # sample every 16th launch of each kernel with CUDA events
+
+
+def _env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+def _config(world: int) -> dict:
+    return {"workload": f"{WORKLOAD}: TV + z-smoothness PnP-ADMM, 512x512x16, "
+                        f"{PARAMS['iters']} iterations, {PARAMS['tv_inner']} TV steps",
+            "volume": [16, 512, 512], "iterations": PARAMS["iters"],
+            "tv_inner": PARAMS["tv_inner"], "rho": PARAMS["rho"], "lambda": PARAMS["lam"],
+            "gamma": PARAMS["gamma"], "l2": "flushed between steps (512 MiB write)",
+            "parallelism": f"replicas x{world}"}
+
+
+def tv_flops_per_launch(H: int, W: int, T: int) -> float:
+    """Algorithmic FP32 operations of one single-slice TV-prox launch.
+
+    Per pixel and Chambolle step: q = div p - g/theta (5), grad q (2),
+    |grad q| (3 + sqrt = 4), 1 + tau|.| (2), two p updates (2 x 3) = 19;
+    per pixel once: g from w and the two z neighbours (5) and
+    u = g - theta div p with d = w - u (6) = 11.
+    """
+    return float(H * W) * (19.0 * T + 11.0)
+
+
+def alu_peak_tflops(sm_mhz: float) -> float:
+    """FP32 FMA peak: 152 SMs x 128 lanes x 2 flops x clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def _kernel_hash() -> str:
+    p = os.path.join(ROOT, "paper_2511_03093_gb300", "csrc", "kernels_tv.cu")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+def _traffic():
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary,
+    if it was taken on the kernel source as it is now."""
+    p = os.path.join(ROOT, "profiles", "tv_tile_tvz_512x512x16.json")
+    try:
+        rec = json.load(open(p))
+    except (OSError, ValueError):
+        return None
+    if rec.get("kernels_tv_sha256_16") != _kernel_hash():
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "100"]
+        if gpu_id:
+            cmd += ["-i", gpu_id]
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[4:8]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, x in enumerate(r)
+                          if x.lower() == "active"})
+        loaded = [s for s, _, _ in rows]
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(m for _, m, _ in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(data, iters: int) -> dict:
+    import oracle
+
+    t0 = time.perf_counter()
+    oracle.admm(data["b64"], data["masks"], 16, rho=PARAMS["rho"], lam=PARAMS["lam"],
+                gamma=PARAMS["gamma"], iters=iters, denoiser="tv", tv_inner=PARAMS["tv_inner"],
+                tv_tau=PARAMS["tv_tau"])
+    dt = time.perf_counter() - t0
+    vox = data["masks"].size
+    return {"value": vox * iters / dt, "unit": UNIT, "cores": _omp_threads(), "kind": "oracle",
+            "sample": f"FP64 oracle, {iters} ADMM iterations of the 512x512x16 TV + z solve "
+                      f"({dt:.1f} s)"}
+
+
+def _omp_threads() -> int:
+    return int(os.environ.get("OMP_NUM_THREADS", len(os.sched_getaffinity(0))))
+
+
+def run_reference(args) -> None:
+    """The FP64 CPU oracle as the reference arm (rank 0 only)."""
+    if _env_int("RANK", 0) != 0:
+        return
+    import synth
+
+    data = synth.generate(WORKLOAD)
+    import oracle
+
+    oracle.lib()
+    iters = 20  # bounded sample per step: 20 of the 100 ADMM iterations
+    vox = data["masks"].size
+
+    def step():
+        t0 = time.perf_counter()
+        oracle.admm(data["b64"], data["masks"], 16, rho=PARAMS["rho"], lam=PARAMS["lam"],
+                    gamma=PARAMS["gamma"], iters=iters, denoiser="tv",
+                    tv_inner=PARAMS["tv_inner"], tv_tau=PARAMS["tv_tau"])
+        return time.perf_counter() - t0
+
+    for _ in range(args.warmup):
+        step()
+    ts = [step() for _ in range(args.steps)]
+    total = sum(ts)
+    value = vox * iters * args.steps / total
+    sample = f"FP64 oracle, {iters} of {PARAMS['iters']} ADMM iterations per step"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": _config(1),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": _omp_threads(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def run_ours(args) -> None:
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    import paper_2511_03093_gb300 as cs
+
+    rank, world = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1)
+    local = _env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    cs.lib()
+
+    w = synth.WORKLOADS[WORKLOAD]
+    if rank:
+        import dataclasses
+
+        w = dataclasses.replace(w, seed=w.seed + 100 * rank)
+    data = synth.generate(w)
+    prm = cs.Params(**PARAMS)
+    vox = w.Z * w.H * w.W
+    masks_h = torch.from_numpy(data["masks"]).pin_memory()
+    b_h = torch.from_numpy(data["b"]).pin_memory()
+    v_h = torch.empty((w.Z, w.H, w.W), dtype=torch.float32).pin_memory()
+    masks_d = masks_h.to(dev)
+    b_d = b_h.to(dev)
+    v_d = torch.empty((w.Z, w.H, w.W), dtype=torch.float32, device=dev)
+    plan = cs.Plan(w.H, w.W, 1, w.Z, masks_d)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        plan.set_masks(masks_d)
+        plan.solve(b_d, prm, v_out=v_d)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+
+    gpu_id = None
+    try:
+        gpu_id = str(torch.cuda.get_device_properties(dev).uuid)
+        if gpu_id and not gpu_id.startswith("GPU-"):
+            gpu_id = "GPU-" + gpu_id
+    except Exception:
+        gpu_id = None
+    ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    cs.timing_read(DOMINANT, reset=True)
+    clocks = ClockSampler(gpu_id) if rank == 0 else None
+
+    barrier()
+    torch.cuda.synchronize()
+    n0 = cs.launch_count()
+    cs.timing_enable(TIMING_PERIOD)
+    for k in range(args.steps):
+        flush.zero_()
+        ev_s[k].record(stream)
+        step()
+        ev_e[k].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    cs.timing_enable(0)
+    launches = cs.launch_count() - n0
+    clk = clocks.stop() if clocks else None
+    step_ms = [ev_s[k].elapsed_time(ev_e[k]) for k in range(args.steps)]
+    total_ms = sum(step_ms)
+    n_dom, ms_dom = cs.timing_read(DOMINANT, reset=True)
+
+    # end to end through the public API: host inputs in, host result out
+    e2e_ms = []
+    for k in range(args.steps):
+        flush.zero_()
+        s_ev, e_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s_ev.record(stream)
+        masks_d.copy_(masks_h, non_blocking=True)
+        b_d.copy_(b_h, non_blocking=True)
+        step()
+        v_h.copy_(v_d, non_blocking=True)
+        e_ev.record(stream)
+        e_ev.synchronize()
+        e2e_ms.append(s_ev.elapsed_time(e_ev))
+    e2e_total = sum(e2e_ms)
+
+    t = torch.tensor([total_ms, e2e_total], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms, e2e_total = float(t[0]), float(t[1])
+    units = vox * PARAMS["iters"] * args.steps * world
+    value = units / (total_ms / 1e3)
+    e2e_value = units / (e2e_total / 1e3)
+
+    if rank == 0:
+        sm_max = (clk or {}).get("sm_max_mhz") or 2070.0
+        roof = None
+        if n_dom:
+            avg_s = ms_dom / n_dom / 1e3
+            achieved = tv_flops_per_launch(w.H, w.W, PARAMS["tv_inner"]) / avg_s / 1e12
+            peak = alu_peak_tflops(sm_max)
+            roof = {"bound": "alu", "kernel": DOMINANT, "achieved": achieved, "peak": peak,
+                    "unit": "TFLOP/s", "frac": achieved / peak, "traffic": _traffic(),
+                    "avg_launch_us": avg_s * 1e6, "launches_timed": n_dom,
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
+                    "share_of_step": ms_dom * TIMING_PERIOD / total_ms}
+        cpu = cpu_baseline(data, PARAMS["iters"]) if world == 1 or rank == 0 else None
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded Gaussian-blob volumes, Bernoulli DMD masks)",
+            "config": _config(world), "roofline": roof, "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT,
+                    "h2d_bytes_per_step": int(masks_h.numel() + b_h.numel() * 4),
+                    "d2h_bytes_per_step": int(v_h.numel() * 4)},
+            "gpu_launches": int(launches), "clocks": clk,
+            "step_ms": [round(x, 3) for x in step_ms],
+        }
+        print(json.dumps(out), flush=True)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

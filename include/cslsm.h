@@ -1,0 +1,185 @@
+/*
+ * cslsm: GB300-native PnP-ADMM reconstruction for compressive light-sheet
+ * microscopy (Gong, Zhang, Chai, Ding, Lou, arXiv 2511.03093).
+ *
+ * C ABI.  Plain pointers and sizes only.  Conventions shared by every call:
+ *
+ *  - Layout.  Volumes (v, u, d, denoiser in/out) are float32 [Z][H][W],
+ *    row-major with W fastest; Z = n_shots * R and slice n = j*R + r belongs
+ *    to shot j, plane r (Sec. III-A).  Measurements b are float32
+ *    [n_shots][H][W].  Masks are uint8 [R][H][W] (one pattern set shared by
+ *    every shot, phi_r of Eq. model-slice) or [Z][H][W] (one pattern per
+ *    slice); any nonzero byte is an open DMD mirror.
+ *  - Memory.  Every data pointer is DEVICE memory owned by the caller, on the
+ *    current CUDA device, unless the argument says "host".  The library keeps
+ *    no pointer to caller memory after a call returns; a plan owns its own
+ *    device workspace.
+ *  - Streams.  `stream` is a cudaStream_t (NULL = legacy default stream).
+ *    Work is enqueued asynchronously on it; a call returns before the GPU has
+ *    finished unless its comment says it synchronises.  Caller buffers must
+ *    stay valid until the stream reaches the enqueued work.
+ *  - Errors.  Every call returns a cslsm_status and never throws or exits.
+ *    Argument checks happen before any GPU work is enqueued (nothing is
+ *    launched on CSLSM_ERR_INVALID_ARG / CSLSM_ERR_UNSUPPORTED);
+ *    cslsm_last_error() gives a per-thread message for the last failure.
+ *  - Limits.  1 <= R <= CSLSM_MAX_R planes per shot; H, W >= 1;
+ *    Z * H * W < 2^31.
+ */
+#ifndef CSLSM_H
+#define CSLSM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CSLSM_MAX_R 32
+#define CSLSM_ABI_VERSION 1
+
+typedef enum {
+    CSLSM_OK = 0,
+    CSLSM_ERR_INVALID_ARG = 1, /* bad pointer, size, parameter or shape */
+    CSLSM_ERR_CUDA = 2,        /* a CUDA runtime call or kernel launch failed */
+    CSLSM_ERR_TIMEOUT = 3,     /* a bounded device-side wait gave up */
+    CSLSM_ERR_UNSUPPORTED = 4, /* valid request this build does not implement */
+    CSLSM_ERR_OOM = 5          /* device allocation failed */
+} cslsm_status;
+
+/* The plug-in priors of the u-step (Eq. u-sub, Sec. III-B). */
+typedef enum {
+    CSLSM_DEN_TIKHONOV = 0, /* psi(u) = ||u||^2, closed form (Sec. III-B, III-C) */
+    CSLSM_DEN_TV = 1,       /* isotropic TV, Chambolle dual projection */
+    CSLSM_DEN_BM3D = 2      /* block matching + 3D collaborative filtering */
+} cslsm_denoiser;
+
+/* Parameters of Algorithm 1 and of its denoiser.
+ *   rho     > 0   ADMM penalty (augmented Lagrangian of Sec. III-B).
+ *   lambda  >= 0  prior weight (Eq. model-slice).  Ignored by BM3D, whose
+ *                 strength is bm3d_sigma (the paper's "noise level" lambda).
+ *   gamma   >= 0  z-smoothness weight (Sec. III-C); 0 = slice-based model.
+ *                 Ignored when Z == 1.
+ *   iters   >= 0  maximum number of ADMM iterations.
+ *   tol     >= 0  stop once ||v^{k+1}-v^k|| / ||v^k|| < tol (checked every
+ *                 check_every iterations; the check synchronises the stream).
+ *                 0 runs exactly `iters` iterations without synchronising.
+ *   check_every   >= 1, used only when tol > 0.
+ *   denoiser      a cslsm_denoiser.
+ *   tv_inner      TV: Chambolle steps per prox (>= 1).
+ *   tv_tau        TV: dual step, 0 < tv_tau <= 0.25 (1/8 is the convergent
+ *                 bound of Chambolle 2004).
+ *   bm3d_sigma    BM3D: noise standard deviation on the volume's scale (> 0).
+ *   init_user     0: u^0 = d^0 = 0.  1: u_io / d_io hold u^0, d^0. */
+typedef struct {
+    float rho;
+    float lambda;
+    float gamma;
+    int iters;
+    float tol;
+    int check_every;
+    int denoiser;
+    int tv_inner;
+    float tv_tau;
+    float bm3d_sigma;
+    int init_user;
+} cslsm_admm_params;
+
+/* Filled by cslsm_admm_solve when non-NULL (host memory). */
+typedef struct {
+    int iters_done;    /* ADMM iterations executed */
+    double rel_change; /* last ||v^{k+1}-v^k||/||v^k|| when tol > 0, else -1 */
+} cslsm_admm_stats;
+
+typedef struct cslsm_plan_s *cslsm_plan;
+
+/* Create a plan for one acquisition geometry and DMD pattern set (Sec. III-A).
+ *   plan      out (host): receives the opaque handle.
+ *   H, W      image size; n_shots >= 1 coded images of R planes each.
+ *   masks     device uint8, [R][H][W] if per_slice == 0 or [Z][H][W] if 1.
+ * The plan packs the patterns into one R-bit word per pixel and shot (bit r
+ * = mirror open for plane r; diag(Phi Phi^T) is its popcount, Sec. III-B) and
+ * allocates its workspace (about 3 * Z*H*W floats).  Synchronises `stream`. */
+cslsm_status cslsm_plan_create(cslsm_plan *plan, int H, int W, int n_shots, int R,
+                               const uint8_t *masks, int per_slice, void *stream);
+
+/* Replace the plan's DMD patterns (same geometry): re-packs the bit words.
+ * Asynchronous; later calls on the same stream see the new patterns. */
+cslsm_status cslsm_plan_set_masks(cslsm_plan plan, const uint8_t *masks, int per_slice,
+                                  void *stream);
+
+/* Release the plan and its device memory.  Synchronises the device first.
+ * NULL is accepted. */
+cslsm_status cslsm_plan_destroy(cslsm_plan plan);
+
+/* Forward operator (Sec. III-A, Eq. model-slice):
+ *   b_j = sum_r phi_r (.) v_{jR+r}.   v: [Z][H][W] in, b: [n_shots][H][W] out. */
+cslsm_status cslsm_forward(cslsm_plan plan, const float *v, float *b, void *stream);
+
+/* Adjoint (Phi^T of Eq. v-update): v_{jR+r} = phi_r (.) b_j.
+ *   b: [n_shots][H][W] in, v: [Z][H][W] out. */
+cslsm_status cslsm_adjoint(cslsm_plan plan, const float *b, float *v, void *stream);
+
+/* Algorithm 1 (CS LSM temporal reconstruction; gamma = 0 is the slice-based
+ * method): per iteration the Woodbury-form v-update of Eq. (v-update), the
+ * Gauss-Seidel u-sweep of Eq. (u-update) with the chosen denoiser, and the
+ * dual update d <- d + v - u (Eq. ADMM).
+ *   b       device [n_shots][H][W] measurement.
+ *   v_out   device [Z][H][W]: receives v^K, Algorithm 1's output.
+ *   u_io, d_io  device [Z][H][W] or NULL.  When given they are the ADMM
+ *           state (read as u^0, d^0 if init_user, always written with u^K,
+ *           d^K), which lets a caller resume a solve; when NULL the plan's
+ *           own state buffers are used (then init_user must be 0).
+ *   stats   host, optional.
+ * v_out must not overlap u_io, d_io or b. */
+cslsm_status cslsm_admm_solve(cslsm_plan plan, const float *b, const cslsm_admm_params *params,
+                              float *v_out, float *u_io, float *d_io, cslsm_admm_stats *stats,
+                              void *stream);
+
+/* The u-step denoiser alone, slice by slice, without z coupling (Eq. u-sub):
+ *   Tikhonov: out = rho * in / (2 lambda + rho);
+ *   TV:       out = argmin theta*TV(u) + 1/2||u - in||^2, theta = lambda / rho,
+ *             by params->tv_inner Chambolle steps from p = 0;
+ *   BM3D:     out = BM3D(in) at noise level params->bm3d_sigma.
+ * in, out: device [Z][H][W]; they must not overlap (neighbour reads). */
+cslsm_status cslsm_denoise(int denoiser, const float *in, float *out, int Z, int H, int W,
+                           const cslsm_admm_params *params, void *stream);
+
+/* Volume PSNR of Sec. IV (all voxels as one array): writes
+ * 10 log10(n V^2 / ||x - ref||^2), V = max(ref), as a double to out (device).
+ * Deterministic two-level reduction; uses a stream-ordered scratch buffer. */
+cslsm_status cslsm_psnr(const float *x, const float *ref, size_t n, double *out, void *stream);
+
+/* Human-readable name of a status code (static string). */
+const char *cslsm_status_string(cslsm_status status);
+
+/* Message describing the calling thread's most recent failure ("" if none). */
+const char *cslsm_last_error(void);
+
+/* CSLSM_ABI_VERSION of the loaded library. */
+int cslsm_abi_version(void);
+
+/* ---- instrumentation (benchmarks, tracing) ------------------------------ */
+
+/* Number of kernels the library has launched in this process so far. */
+unsigned long long cslsm_launch_count(void);
+
+/* Sampled kernel timing.  period > 0: from now on every period-th launch of
+ * each kernel is bracketed by two CUDA events recorded on its stream (the
+ * events add a little GPU time of their own); 0 switches sampling off.
+ * Kernel names: "pack_masks", "forward", "adjoint", "xupdate_w",
+ * "tikhonov_iter", "tikhonov_prox", "tv_tile", "psnr_partials",
+ * "reduce_finish". */
+cslsm_status cslsm_timing_enable(int period);
+
+/* Waits for the recorded events of `kernel` and returns how many launches
+ * were timed and their summed device time in milliseconds (host pointers).
+ * reset != 0 then discards every record of every kernel and restarts the
+ * sampling counters. */
+cslsm_status cslsm_timing_read(const char *kernel, long long *launches_timed, double *total_ms,
+                               int reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CSLSM_H */

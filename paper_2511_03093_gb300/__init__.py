@@ -1,0 +1,257 @@
+"""Python binding of libcslsm, the GB300 PnP-ADMM light-sheet reconstruction.
+
+Argument marshalling only: every step of the reconstruction runs in the CUDA
+kernels of libcslsm.so (built in-tree for sm_103a by ``build.py``).  PyTorch
+provides device memory and streams; tensors are passed to the C ABI as raw
+device pointers together with the current CUDA stream.
+
+There is no CPU path: importing the package works without a GPU, but every
+call that computes raises if the shared library is missing or no CUDA device
+is present.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcslsm.so")
+
+TIKHONOV, TV, BM3D = 0, 1, 2
+DENOISERS = {"tikhonov": TIKHONOV, "tv": TV, "bm3d": BM3D}
+MAX_R = 32
+
+STATUS = {0: "CSLSM_OK", 1: "CSLSM_ERR_INVALID_ARG", 2: "CSLSM_ERR_CUDA",
+          3: "CSLSM_ERR_TIMEOUT", 4: "CSLSM_ERR_UNSUPPORTED", 5: "CSLSM_ERR_OOM"}
+
+
+class CslsmError(RuntimeError):
+    def __init__(self, status: int, func: str, msg: str):
+        self.status = status
+        super().__init__(f"{func}: {STATUS.get(status, status)}: {msg}")
+
+
+class AdmmParams(ctypes.Structure):
+    """Mirror of cslsm_admm_params (include/cslsm.h)."""
+
+    _fields_ = [("rho", ctypes.c_float), ("lambda_", ctypes.c_float),
+                ("gamma", ctypes.c_float), ("iters", ctypes.c_int), ("tol", ctypes.c_float),
+                ("check_every", ctypes.c_int), ("denoiser", ctypes.c_int),
+                ("tv_inner", ctypes.c_int), ("tv_tau", ctypes.c_float),
+                ("bm3d_sigma", ctypes.c_float), ("init_user", ctypes.c_int)]
+
+
+class AdmmStats(ctypes.Structure):
+    _fields_ = [("iters_done", ctypes.c_int), ("rel_change", ctypes.c_double)]
+
+
+@dataclasses.dataclass
+class Params:
+    """Algorithm-1 parameters (see cslsm_admm_params in include/cslsm.h)."""
+
+    rho: float = 1.0
+    lam: float = 0.05
+    gamma: float = 0.0
+    iters: int = 50
+    denoiser: str = "tv"
+    tol: float = 0.0
+    check_every: int = 1
+    tv_inner: int = 20
+    tv_tau: float = 0.125
+    bm3d_sigma: float = 0.05
+
+    def to_c(self, init_user: bool = False) -> AdmmParams:
+        return AdmmParams(float(self.rho), float(self.lam), float(self.gamma), int(self.iters),
+                          float(self.tol), int(self.check_every), DENOISERS[self.denoiser],
+                          int(self.tv_inner), float(self.tv_tau), float(self.bm3d_sigma),
+                          int(bool(init_user)))
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libcslsm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libcslsm.so not built ({LIB_PATH}); run "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`")
+    L = ctypes.CDLL(LIB_PATH)
+    P, I, F = ctypes.c_void_p, ctypes.c_int, ctypes.c_float
+    sigs = {
+        "cslsm_plan_create": [ctypes.POINTER(P), I, I, I, I, P, I, P],
+        "cslsm_plan_set_masks": [P, P, I, P],
+        "cslsm_plan_destroy": [P],
+        "cslsm_forward": [P, P, P, P],
+        "cslsm_adjoint": [P, P, P, P],
+        "cslsm_admm_solve": [P, P, ctypes.POINTER(AdmmParams), P, P, P,
+                             ctypes.POINTER(AdmmStats), P],
+        "cslsm_denoise": [I, P, P, I, I, I, ctypes.POINTER(AdmmParams), P],
+        "cslsm_psnr": [P, P, ctypes.c_size_t, P, P],
+    }
+    for name, args in sigs.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = I
+    L.cslsm_status_string.argtypes = [I]
+    L.cslsm_status_string.restype = ctypes.c_char_p
+    L.cslsm_last_error.argtypes = []
+    L.cslsm_last_error.restype = ctypes.c_char_p
+    L.cslsm_abi_version.argtypes = []
+    L.cslsm_abi_version.restype = I
+    L.cslsm_launch_count.argtypes = []
+    L.cslsm_launch_count.restype = ctypes.c_ulonglong
+    L.cslsm_timing_enable.argtypes = [I]
+    L.cslsm_timing_enable.restype = I
+    L.cslsm_timing_read.argtypes = [ctypes.c_char_p, ctypes.POINTER(ctypes.c_longlong),
+                                    ctypes.POINTER(ctypes.c_double), I]
+    L.cslsm_timing_read.restype = I
+    _lib = L
+    return L
+
+
+def _check(status: int, func: str) -> None:
+    if status != 0:
+        raise CslsmError(status, func, lib().cslsm_last_error().decode())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev(t: torch.Tensor, name: str, dtype: torch.dtype, shape=None):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Plan:
+    """An acquisition geometry with its packed DMD patterns (cslsm_plan)."""
+
+    def __init__(self, H: int, W: int, n_shots: int, R: int, masks: torch.Tensor,
+                 per_slice: bool = True, stream=None):
+        self.H, self.W, self.N, self.R = int(H), int(W), int(n_shots), int(R)
+        self.Z = self.N * self.R
+        self.per_slice = bool(per_slice)
+        self._h = ctypes.c_void_p()
+        mp = _dev(masks, "masks", torch.uint8,
+                  (self.Z if per_slice else self.R, self.H, self.W))
+        _check(lib().cslsm_plan_create(ctypes.byref(self._h), self.H, self.W, self.N, self.R,
+                                       mp, int(self.per_slice), _stream(stream)),
+               "cslsm_plan_create")
+
+    @property
+    def vol_shape(self):
+        return (self.Z, self.H, self.W)
+
+    @property
+    def meas_shape(self):
+        return (self.N, self.H, self.W)
+
+    def set_masks(self, masks: torch.Tensor, stream=None) -> None:
+        mp = _dev(masks, "masks", torch.uint8,
+                  (self.Z if self.per_slice else self.R, self.H, self.W))
+        _check(lib().cslsm_plan_set_masks(self._h, mp, int(self.per_slice), _stream(stream)),
+               "cslsm_plan_set_masks")
+
+    def forward(self, v: torch.Tensor, b: torch.Tensor | None = None, stream=None):
+        if b is None:
+            b = torch.empty(self.meas_shape, dtype=torch.float32, device=v.device)
+        _check(lib().cslsm_forward(self._h, _dev(v, "v", torch.float32, self.vol_shape),
+                                   _dev(b, "b", torch.float32, self.meas_shape),
+                                   _stream(stream)), "cslsm_forward")
+        return b
+
+    def adjoint(self, b: torch.Tensor, v: torch.Tensor | None = None, stream=None):
+        if v is None:
+            v = torch.empty(self.vol_shape, dtype=torch.float32, device=b.device)
+        _check(lib().cslsm_adjoint(self._h, _dev(b, "b", torch.float32, self.meas_shape),
+                                   _dev(v, "v", torch.float32, self.vol_shape),
+                                   _stream(stream)), "cslsm_adjoint")
+        return v
+
+    def solve(self, b: torch.Tensor, params: Params, v_out: torch.Tensor | None = None,
+              u: torch.Tensor | None = None, d: torch.Tensor | None = None,
+              init_user: bool = False, stream=None, stats: bool = False):
+        """Algorithm 1; returns v^K (and the cslsm_admm_stats fields if stats)."""
+        if v_out is None:
+            v_out = torch.empty(self.vol_shape, dtype=torch.float32, device=b.device)
+        up = _dev(u, "u", torch.float32, self.vol_shape) if u is not None else None
+        dp = _dev(d, "d", torch.float32, self.vol_shape) if d is not None else None
+        st = AdmmStats()
+        cp = params.to_c(init_user)
+        _check(lib().cslsm_admm_solve(self._h, _dev(b, "b", torch.float32, self.meas_shape),
+                                      ctypes.byref(cp), _dev(v_out, "v_out", torch.float32,
+                                                             self.vol_shape),
+                                      up, dp, ctypes.byref(st), _stream(stream)),
+               "cslsm_admm_solve")
+        if stats:
+            return v_out, {"iters_done": st.iters_done, "rel_change": st.rel_change}
+        return v_out
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) and self._h.value:
+            _check(lib().cslsm_plan_destroy(self._h), "cslsm_plan_destroy")
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def denoise(x: torch.Tensor, params: Params, out: torch.Tensor | None = None, stream=None):
+    """The u-step prior alone on each slice of x [Z,H,W] (cslsm_denoise)."""
+    if x.dim() == 2:
+        x = x[None]
+    Z, H, W = x.shape
+    if out is None:
+        out = torch.empty_like(x)
+    cp = params.to_c()
+    _check(lib().cslsm_denoise(cp.denoiser, _dev(x, "x", torch.float32),
+                               _dev(out, "out", torch.float32, (Z, H, W)), Z, H, W,
+                               ctypes.byref(cp), _stream(stream)), "cslsm_denoise")
+    return out
+
+
+def psnr(x: torch.Tensor, ref: torch.Tensor, stream=None) -> torch.Tensor:
+    """Volume PSNR (Sec. IV) as a 1-element float64 CUDA tensor."""
+    if x.shape != ref.shape:
+        raise ValueError("x and ref must have the same shape")
+    out = torch.empty(1, dtype=torch.float64, device=x.device)
+    _check(lib().cslsm_psnr(_dev(x, "x", torch.float32), _dev(ref, "ref", torch.float32),
+                            x.numel(), ctypes.c_void_p(out.data_ptr()), _stream(stream)),
+           "cslsm_psnr")
+    return out
+
+
+def launch_count() -> int:
+    """Kernels launched by libcslsm in this process so far."""
+    return int(lib().cslsm_launch_count())
+
+
+def timing_enable(period: int) -> None:
+    """Sample every period-th launch of each kernel with CUDA events (0: off)."""
+    _check(lib().cslsm_timing_enable(int(period)), "cslsm_timing_enable")
+
+
+def timing_read(kernel: str, reset: bool = False) -> tuple[int, float]:
+    """(launches timed, summed device milliseconds) for one kernel name."""
+    n = ctypes.c_longlong()
+    ms = ctypes.c_double()
+    _check(lib().cslsm_timing_read(kernel.encode(), ctypes.byref(n), ctypes.byref(ms),
+                                   int(bool(reset))), "cslsm_timing_read")
+    return int(n.value), float(ms.value)

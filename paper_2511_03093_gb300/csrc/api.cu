@@ -1,0 +1,418 @@
+// C ABI of libcslsm: argument checking, plan / workspace ownership and the
+// host-side schedule of Algorithm 1.  All arithmetic runs in the kernels of
+// kernels_pointwise.cu and kernels_tv.cu.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "internal.cuh"
+
+namespace cslsm {
+
+namespace {
+thread_local char g_last_error[512] = "";
+}
+
+void set_error(const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+    va_end(ap);
+}
+
+}  // namespace cslsm
+
+using namespace cslsm;
+
+struct cslsm_plan_s {
+    Geom g;
+    int device;
+    int per_slice;
+    uint32_t *words = nullptr;  // [nsets][H][W]
+    int nsets = 0;
+    float *u = nullptr, *d = nullptr, *w = nullptr;  // [Z][H][W] state and workspace
+    float *vprev = nullptr;                          // [Z][H][W], tolerance checks only
+    float *pbuf = nullptr;                           // TV dual buffers for long proxes
+    size_t pbuf_floats = 0;
+    double *partials = nullptr;  // reduction partials (2 doubles per block)
+    int npartials = 0;
+    double *red_out = nullptr;  // 2 doubles
+};
+
+namespace {
+
+#define CHECK_ARG(cond, ...)                    \
+    do {                                        \
+        if (!(cond)) {                          \
+            set_error(__VA_ARGS__);             \
+            return CSLSM_ERR_INVALID_ARG;       \
+        }                                       \
+    } while (0)
+
+inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+bool finite_f(float x) { return std::isfinite(x); }
+
+cslsm_status check_geometry(int H, int W, int N, int R)
+{
+    CHECK_ARG(H >= 1 && W >= 1, "H and W must be >= 1 (got %d, %d)", H, W);
+    CHECK_ARG(N >= 1, "n_shots must be >= 1 (got %d)", N);
+    CHECK_ARG(R >= 1 && R <= CSLSM_MAX_R, "R must be in [1, %d] (got %d)", CSLSM_MAX_R, R);
+    const long long v = (long long)N * R * H * W;
+    CHECK_ARG(v < (1ll << 31), "Z*H*W must be < 2^31 (got %lld)", v);
+    return CSLSM_OK;
+}
+
+cslsm_status check_params(const cslsm_admm_params *p, bool for_denoise)
+{
+    CHECK_ARG(p != nullptr, "params is NULL");
+    CHECK_ARG(finite_f(p->rho) && p->rho > 0.f, "rho must be finite and > 0");
+    CHECK_ARG(finite_f(p->lambda) && p->lambda >= 0.f, "lambda must be finite and >= 0");
+    CHECK_ARG(p->denoiser >= CSLSM_DEN_TIKHONOV && p->denoiser <= CSLSM_DEN_BM3D,
+              "unknown denoiser %d", p->denoiser);
+    if (p->denoiser == CSLSM_DEN_TV) {
+        CHECK_ARG(p->tv_inner >= 1, "tv_inner must be >= 1");
+        CHECK_ARG(finite_f(p->tv_tau) && p->tv_tau > 0.f && p->tv_tau <= 0.25f,
+                  "tv_tau must be in (0, 0.25]");
+    }
+    if (p->denoiser == CSLSM_DEN_BM3D)
+        CHECK_ARG(finite_f(p->bm3d_sigma) && p->bm3d_sigma > 0.f, "bm3d_sigma must be > 0");
+    if (for_denoise) return CSLSM_OK;
+    CHECK_ARG(finite_f(p->gamma) && p->gamma >= 0.f, "gamma must be finite and >= 0");
+    CHECK_ARG(p->iters >= 0, "iters must be >= 0");
+    CHECK_ARG(finite_f(p->tol) && p->tol >= 0.f, "tol must be finite and >= 0");
+    if (p->tol > 0.f) CHECK_ARG(p->check_every >= 1, "check_every must be >= 1 when tol > 0");
+    CHECK_ARG(p->init_user == 0 || p->init_user == 1, "init_user must be 0 or 1");
+    return CSLSM_OK;
+}
+
+cslsm_status check_device(const cslsm_plan_s *plan)
+{
+    int dev = -1;
+    CSLSM_CUDA(cudaGetDevice(&dev));
+    CHECK_ARG(dev == plan->device, "plan belongs to device %d, current device is %d",
+              plan->device, dev);
+    return CSLSM_OK;
+}
+
+Masks masks_of(const cslsm_plan_s *p) { return Masks{p->words, p->nsets > 1 ? p->g.HW() : 0}; }
+
+void free_plan(cslsm_plan_s *p)
+{
+    cudaFree(p->words);
+    cudaFree(p->u);
+    cudaFree(p->d);
+    cudaFree(p->w);
+    cudaFree(p->vprev);
+    cudaFree(p->pbuf);
+    cudaFree(p->partials);
+    cudaFree(p->red_out);
+    delete p;
+}
+
+cslsm_status pack(cslsm_plan_s *p, const uint8_t *masks, int per_slice, cudaStream_t s)
+{
+    const int nsets = per_slice ? p->g.N : 1;
+    CHECK_ARG(nsets == p->nsets || p->nsets == 0,
+              "per_slice changes the number of pattern sets; create a new plan");
+    return launch_pack_masks(masks, p->words, p->g.HW(), p->g.R, nsets, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+int cslsm_abi_version(void) { return CSLSM_ABI_VERSION; }
+
+const char *cslsm_status_string(cslsm_status st)
+{
+    switch (st) {
+    case CSLSM_OK: return "CSLSM_OK";
+    case CSLSM_ERR_INVALID_ARG: return "CSLSM_ERR_INVALID_ARG";
+    case CSLSM_ERR_CUDA: return "CSLSM_ERR_CUDA";
+    case CSLSM_ERR_TIMEOUT: return "CSLSM_ERR_TIMEOUT";
+    case CSLSM_ERR_UNSUPPORTED: return "CSLSM_ERR_UNSUPPORTED";
+    case CSLSM_ERR_OOM: return "CSLSM_ERR_OOM";
+    }
+    return "CSLSM_STATUS_UNKNOWN";
+}
+
+const char *cslsm_last_error(void) { return g_last_error; }
+
+cslsm_status cslsm_plan_create(cslsm_plan *out, int H, int W, int n_shots, int R,
+                               const uint8_t *masks, int per_slice, void *stream)
+{
+    CHECK_ARG(out != nullptr, "plan output pointer is NULL");
+    *out = nullptr;
+    cslsm_status st = check_geometry(H, W, n_shots, R);
+    if (st) return st;
+    CHECK_ARG(masks != nullptr, "masks is NULL");
+    CHECK_ARG(per_slice == 0 || per_slice == 1, "per_slice must be 0 or 1");
+    cslsm_plan_s *p = new (std::nothrow) cslsm_plan_s();
+    CHECK_ARG(p != nullptr, "host allocation failed");
+    p->g = Geom{H, W, n_shots, R};
+    p->per_slice = per_slice;
+    p->nsets = per_slice ? n_shots : 1;
+    const size_t nv = (size_t)p->g.voxels();
+    const dim3 grid_px((p->g.HW() + 255) / 256, n_shots);
+    p->npartials = (int)(grid_px.x * grid_px.y);
+    cudaStream_t s = as_stream(stream);
+#define TRY(call)                                                                           \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess) {                                                            \
+            set_error("%s failed: %s", #call, cudaGetErrorString(e_));                      \
+            free_plan(p);                                                                   \
+            return e_ == cudaErrorMemoryAllocation ? CSLSM_ERR_OOM : CSLSM_ERR_CUDA;        \
+        }                                                                                   \
+    } while (0)
+    TRY(cudaGetDevice(&p->device));
+    TRY(cudaMalloc(&p->words, sizeof(uint32_t) * (size_t)p->nsets * p->g.HW()));
+    TRY(cudaMalloc(&p->u, sizeof(float) * nv));
+    TRY(cudaMalloc(&p->d, sizeof(float) * nv));
+    TRY(cudaMalloc(&p->w, sizeof(float) * nv));
+    TRY(cudaMalloc(&p->partials, sizeof(double) * 2 * (size_t)p->npartials));
+    TRY(cudaMalloc(&p->red_out, sizeof(double) * 2));
+#undef TRY
+    st = pack(p, masks, per_slice, s);
+    if (st == CSLSM_OK && cudaStreamSynchronize(s) != cudaSuccess) {
+        set_error("plan_create: %s", cudaGetErrorString(cudaGetLastError()));
+        st = CSLSM_ERR_CUDA;
+    }
+    if (st) {
+        free_plan(p);
+        return st;
+    }
+    *out = p;
+    return CSLSM_OK;
+}
+
+cslsm_status cslsm_plan_set_masks(cslsm_plan plan, const uint8_t *masks, int per_slice,
+                                  void *stream)
+{
+    CHECK_ARG(plan != nullptr, "plan is NULL");
+    CHECK_ARG(masks != nullptr, "masks is NULL");
+    CHECK_ARG(per_slice == 0 || per_slice == 1, "per_slice must be 0 or 1");
+    CHECK_ARG((per_slice ? plan->g.N : 1) == plan->nsets,
+              "per_slice changes the number of pattern sets; create a new plan");
+    cslsm_status st = check_device(plan);
+    if (st) return st;
+    plan->per_slice = per_slice;
+    return pack(plan, masks, per_slice, as_stream(stream));
+}
+
+cslsm_status cslsm_plan_destroy(cslsm_plan plan)
+{
+    if (!plan) return CSLSM_OK;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(plan->device);
+    cudaError_t e = cudaDeviceSynchronize();
+    free_plan(plan);
+    cudaSetDevice(cur);
+    if (e != cudaSuccess) {
+        set_error("plan_destroy: %s", cudaGetErrorString(e));
+        return CSLSM_ERR_CUDA;
+    }
+    return CSLSM_OK;
+}
+
+cslsm_status cslsm_forward(cslsm_plan plan, const float *v, float *b, void *stream)
+{
+    CHECK_ARG(plan != nullptr, "plan is NULL");
+    CHECK_ARG(v != nullptr && b != nullptr, "v and b must be non-NULL");
+    cslsm_status st = check_device(plan);
+    if (st) return st;
+    return launch_forward(plan->g, masks_of(plan), v, b, as_stream(stream));
+}
+
+cslsm_status cslsm_adjoint(cslsm_plan plan, const float *b, float *v, void *stream)
+{
+    CHECK_ARG(plan != nullptr, "plan is NULL");
+    CHECK_ARG(v != nullptr && b != nullptr, "v and b must be non-NULL");
+    cslsm_status st = check_device(plan);
+    if (st) return st;
+    return launch_adjoint(plan->g, masks_of(plan), b, v, as_stream(stream));
+}
+
+cslsm_status cslsm_admm_solve(cslsm_plan plan, const float *b, const cslsm_admm_params *prm,
+                              float *v_out, float *u_io, float *d_io, cslsm_admm_stats *stats,
+                              void *stream)
+{
+    CHECK_ARG(plan != nullptr, "plan is NULL");
+    CHECK_ARG(b != nullptr && v_out != nullptr, "b and v_out must be non-NULL");
+    cslsm_status st = check_params(prm, false);
+    if (st) return st;
+    CHECK_ARG((u_io == nullptr) == (d_io == nullptr), "give both u_io and d_io or neither");
+    CHECK_ARG(!prm->init_user || u_io != nullptr, "init_user needs u_io and d_io");
+    if (prm->denoiser == CSLSM_DEN_BM3D) {
+        set_error("BM3D denoiser is not built in this library");
+        return CSLSM_ERR_UNSUPPORTED;
+    }
+    st = check_device(plan);
+    if (st) return st;
+
+    const Geom &g = plan->g;
+    const size_t nv = (size_t)g.voxels();
+    cudaStream_t s = as_stream(stream);
+    float *u = u_io ? u_io : plan->u;
+    float *d = d_io ? d_io : plan->d;
+    const float gam = g.Z() > 1 ? prm->gamma : 0.f;
+    const bool use_tol = prm->tol > 0.f;
+    if (!prm->init_user) {
+        CSLSM_CUDA(cudaMemsetAsync(u, 0, sizeof(float) * nv, s));
+        CSLSM_CUDA(cudaMemsetAsync(d, 0, sizeof(float) * nv, s));
+    }
+    if (use_tol) {
+        if (!plan->vprev) CSLSM_CUDA(cudaMalloc(&plan->vprev, sizeof(float) * nv));
+        CSLSM_CUDA(cudaMemsetAsync(plan->vprev, 0, sizeof(float) * nv, s));
+    }
+    const bool tv = prm->denoiser == CSLSM_DEN_TV;
+    if (tv && prm->lambda > 0.f && prm->tv_inner > tv_max_steps_per_launch()) {
+        const size_t need = 4 * (gam > 0.f ? 1 : (size_t)g.Z()) * (size_t)g.HW();
+        if (plan->pbuf_floats < need) {
+            CSLSM_CUDA(cudaStreamSynchronize(s));
+            cudaFree(plan->pbuf);
+            plan->pbuf = nullptr;
+            plan->pbuf_floats = 0;
+            CSLSM_CUDA(cudaMalloc(&plan->pbuf, sizeof(float) * need));
+            plan->pbuf_floats = need;
+        }
+    }
+    const Masks m = masks_of(plan);
+    int k = 0;
+    double rel = -1.0;
+    bool stopped = false;
+    for (k = 0; k < prm->iters; ++k) {
+        const bool last = (k == prm->iters - 1);
+        const bool check = use_tol && k > 0 && ((k + 1) % prm->check_every == 0 || last);
+        float *vo = last ? v_out : nullptr;
+        float *vp = use_tol ? plan->vprev : nullptr;
+        double *part = check ? plan->partials : nullptr;
+        if (prm->denoiser == CSLSM_DEN_TIKHONOV) {
+            st = launch_tikhonov_iter(g, m, u, d, b, prm->rho, prm->lambda, gam, vo, vp, part,
+                                      plan->npartials, s);
+            if (st) return st;
+        } else {
+            st = launch_xupdate_w(g, m, u, d, b, prm->rho, plan->w, vo, vp, part,
+                                  plan->npartials, s);
+            if (st) return st;
+            TvSlices a{};
+            a.w = plan->w;
+            a.u = u;
+            a.d = d;
+            a.H = g.H;
+            a.W = g.W;
+            a.Z = g.Z();
+            a.rho = prm->rho;
+            a.gamma = gam;
+            a.theta = prm->lambda / (prm->rho + 2.f * gam);
+            a.tau = prm->tv_tau;
+            a.T = prm->tv_inner;
+            if (gam == 0.f) {
+                a.n0 = 0;
+                a.nslices = g.Z();
+                st = tv_prox_slices(a, plan->pbuf, s);
+                if (st) return st;
+            } else {
+                a.nslices = 1;
+                for (int n = 0; n < g.Z(); ++n) {
+                    a.n0 = n;
+                    st = tv_prox_slices(a, plan->pbuf, s);
+                    if (st) return st;
+                }
+            }
+        }
+        if (check) {
+            const int nblk = prm->denoiser == CSLSM_DEN_TIKHONOV ? (g.HW() + 255) / 256
+                                                                 : plan->npartials;
+            st = launch_sum_pairs(plan->partials, nblk, plan->red_out, s);
+            if (st) return st;
+            double h[2];
+            CSLSM_CUDA(cudaMemcpyAsync(h, plan->red_out, sizeof(h), cudaMemcpyDeviceToHost, s));
+            CSLSM_CUDA(cudaStreamSynchronize(s));
+            rel = h[1] > 0.0 ? std::sqrt(h[0] / h[1]) : INFINITY;
+            if (rel < prm->tol) {
+                stopped = !last;
+                ++k;
+                break;
+            }
+        }
+    }
+    if (stopped)  // v^{k} of the final iteration is in vprev
+        CSLSM_CUDA(cudaMemcpyAsync(v_out, plan->vprev, sizeof(float) * nv,
+                                   cudaMemcpyDeviceToDevice, s));
+    if (prm->iters == 0) {  // v^0: nothing computed; report zeros
+        CSLSM_CUDA(cudaMemsetAsync(v_out, 0, sizeof(float) * nv, s));
+    }
+    if (stats) {
+        stats->iters_done = k;
+        stats->rel_change = use_tol ? rel : -1.0;
+    }
+    return CSLSM_OK;
+}
+
+cslsm_status cslsm_denoise(int denoiser, const float *in, float *out, int Z, int H, int W,
+                           const cslsm_admm_params *prm, void *stream)
+{
+    CHECK_ARG(in != nullptr && out != nullptr, "in and out must be non-NULL");
+    CHECK_ARG(Z >= 1 && H >= 1 && W >= 1, "Z, H, W must be >= 1");
+    CHECK_ARG((long long)Z * H * W < (1ll << 31), "Z*H*W must be < 2^31");
+    cslsm_status st = check_params(prm, true);
+    if (st) return st;
+    CHECK_ARG(denoiser == prm->denoiser, "denoiser argument and params->denoiser differ");
+    const size_t nv = (size_t)Z * H * W;
+    if (denoiser != CSLSM_DEN_TIKHONOV) {
+        const char *a = (const char *)in, *o = (const char *)out;
+        CHECK_ARG(o + nv * sizeof(float) <= a || a + nv * sizeof(float) <= o,
+                  "in and out must not overlap");
+    }
+    cudaStream_t s = as_stream(stream);
+    if (denoiser == CSLSM_DEN_TIKHONOV)
+        return launch_tikhonov_prox(in, out, (long long)nv, prm->rho, prm->lambda, s);
+    if (denoiser == CSLSM_DEN_BM3D) {
+        set_error("BM3D denoiser is not built in this library");
+        return CSLSM_ERR_UNSUPPORTED;
+    }
+    TvSlices a{};
+    a.w = in;
+    a.u = out;
+    a.d = nullptr;
+    a.H = H;
+    a.W = W;
+    a.Z = Z;
+    a.n0 = 0;
+    a.nslices = Z;
+    a.rho = prm->rho;
+    a.gamma = 0.f;
+    a.theta = prm->lambda / prm->rho;
+    a.tau = prm->tv_tau;
+    a.T = prm->tv_inner;
+    float *pbuf = nullptr;
+    if (a.theta > 0.f && a.T > tv_max_steps_per_launch())
+        CSLSM_CUDA(cudaMallocAsync(&pbuf, sizeof(float) * 4 * nv, s));
+    st = tv_prox_slices(a, pbuf, s);
+    if (pbuf) cudaFreeAsync(pbuf, s);
+    return st;
+}
+
+cslsm_status cslsm_psnr(const float *x, const float *ref, size_t n, double *out, void *stream)
+{
+    CHECK_ARG(x != nullptr && ref != nullptr && out != nullptr, "x, ref, out must be non-NULL");
+    CHECK_ARG(n >= 1, "n must be >= 1");
+    cudaStream_t s = as_stream(stream);
+    const int nb = reduction_blocks();
+    double *partials = nullptr;
+    CSLSM_CUDA(cudaMallocAsync(&partials, sizeof(double) * 2 * nb, s));
+    cslsm_status st = launch_psnr_partials(x, ref, n, partials, nb, s);
+    if (!st) st = launch_psnr_finish(partials, nb, n, out, s);
+    cudaFreeAsync(partials, s);
+    return st;
+}
+
+}  // extern "C"

@@ -1,0 +1,407 @@
+// Pixel-local kernels of the PnP-ADMM iteration: DMD pattern packing, the
+// forward / adjoint operators, the Woodbury x-update and the fused Tikhonov
+// iteration, plus deterministic reductions.
+//
+// Layout: volumes [Z][H][W] float32, one thread per pixel column (h, w); the
+// thread walks the R planes of a shot, so every global access of a warp is a
+// contiguous 128-byte row segment of one plane.  The DMD patterns of a shot
+// are one 32-bit word per pixel (bit r = plane r), so diag(Phi Phi^T) at the
+// pixel is __popc(word) (Sec. III-B: Phi Phi^T is diagonal).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.cuh"
+
+namespace cslsm {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kRedBlocks = 1024;
+
+__device__ __forceinline__ bool bit(uint32_t word, int r) { return (word >> r) & 1u; }
+
+__global__ void __launch_bounds__(kThreads) pack_masks_kernel(const uint8_t *__restrict__ masks,
+                                                              uint32_t *__restrict__ words,
+                                                              int HW, int R)
+{
+    const int p = blockIdx.x * kThreads + threadIdx.x;
+    const int j = blockIdx.y;
+    if (p >= HW) return;
+    uint32_t word = 0;
+    const uint8_t *m = masks + (size_t)j * R * HW + p;
+    for (int r = 0; r < R; ++r)
+        word |= (m[(size_t)r * HW] != 0 ? 1u : 0u) << r;
+    words[(size_t)j * HW + p] = word;
+}
+
+// b_j = sum_r phi_r v_{jR+r}  (Sec. III-A)
+__global__ void __launch_bounds__(kThreads) forward_kernel(const float *__restrict__ v,
+                                                           float *__restrict__ b,
+                                                           const uint32_t *__restrict__ words,
+                                                           int wstride, int HW, int R)
+{
+    const int p = blockIdx.x * kThreads + threadIdx.x;
+    const int j = blockIdx.y;
+    if (p >= HW) return;
+    const uint32_t word = words[(size_t)j * wstride + p];
+    const float *vj = v + (size_t)j * R * HW + p;
+    float s = 0.f;
+    for (int r = 0; r < R; ++r)
+        if (bit(word, r)) s += __ldg(vj + (size_t)r * HW);
+    b[(size_t)j * HW + p] = s;
+}
+
+// v_{jR+r} = phi_r b_j
+__global__ void __launch_bounds__(kThreads) adjoint_kernel(const float *__restrict__ b,
+                                                           float *__restrict__ v,
+                                                           const uint32_t *__restrict__ words,
+                                                           int wstride, int HW, int R)
+{
+    const int p = blockIdx.x * kThreads + threadIdx.x;
+    const int j = blockIdx.y;
+    if (p >= HW) return;
+    const uint32_t word = words[(size_t)j * wstride + p];
+    const float bj = b[(size_t)j * HW + p];
+    float *vj = v + (size_t)j * R * HW + p;
+    for (int r = 0; r < R; ++r)
+        vj[(size_t)r * HW] = bit(word, r) ? bj : 0.f;
+}
+
+// Block-wide sum of two doubles; result valid in thread 0.
+__device__ __forceinline__ void block_sum2(double &a, double &c)
+{
+    __shared__ double sa[kThreads / 32], sc[kThreads / 32];
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        c += __shfl_down_sync(0xffffffffu, c, o);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) { sa[wid] = a; sc[wid] = c; }
+    __syncthreads();
+    if (wid == 0) {
+        a = lane < kThreads / 32 ? sa[lane] : 0.0;
+        c = lane < kThreads / 32 ? sc[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_down_sync(0xffffffffu, a, o);
+            c += __shfl_down_sync(0xffffffffu, c, o);
+        }
+    }
+}
+
+// Woodbury x-update (Eq. v-update): for shot j at pixel p,
+//   g_r = u_r - d_r,  e = (b_j - sum_r phi_r g_r) / (rho + popc),
+//   v_r = g_r + phi_r e,  w_r = v_r + d_r.
+template <int RMAX>
+__global__ void __launch_bounds__(kThreads, 2)
+xupdate_w_kernel(const float *__restrict__ u, const float *__restrict__ d,
+                 const float *__restrict__ b, const uint32_t *__restrict__ words, int wstride,
+                 int HW, int R, float rho, float *__restrict__ w, float *__restrict__ v_out,
+                 float *__restrict__ vprev, double *__restrict__ partials)
+{
+    const int p = blockIdx.x * kThreads + threadIdx.x;
+    const int j = blockIdx.y;
+    double sdv = 0.0, sv = 0.0;
+    if (p < HW) {
+        const uint32_t word = words[j * wstride + p];
+        const int base = j * R * HW + p;
+        float g[RMAX], dr[RMAX];
+        float s = 0.f;
+#pragma unroll
+        for (int r = 0; r < RMAX; ++r) {
+            if (r < R) {
+                dr[r] = __ldg(d + base + r * HW);
+                g[r] = __ldg(u + base + r * HW) - dr[r];
+                if (bit(word, r)) s += g[r];
+            }
+        }
+        const float e = (__ldg(b + j * HW + p) - s) / (rho + (float)__popc(word));
+#pragma unroll
+        for (int r = 0; r < RMAX; ++r) {
+            if (r < R) {
+                const int o = base + r * HW;
+                const float v = bit(word, r) ? g[r] + e : g[r];
+                w[o] = v + dr[r];
+                if (v_out) v_out[o] = v;
+                if (vprev) {
+                    const double vp = vprev[o];
+                    sdv += ((double)v - vp) * ((double)v - vp);
+                    sv += vp * vp;
+                    vprev[o] = v;
+                }
+            }
+        }
+    }
+    if (partials) {
+        block_sum2(sdv, sv);
+        if (threadIdx.x == 0) {
+            const int blk = blockIdx.y * gridDim.x + blockIdx.x;
+            partials[2 * blk] = sdv;
+            partials[2 * blk + 1] = sv;
+        }
+    }
+}
+
+// One fused ADMM iteration with the Tikhonov prior (psi = ||u||^2):
+// x-update as above, then along z in order n = 0..Z-1 (Gauss-Seidel, cyclic,
+// always the newest neighbour values)
+//   u_n = (rho w_n + gam (u_{n-1} + u_{n+1})) / (2 lam + rho + 2 gam),
+// and d_n = w_n - u_n  (= d + v - u).  One thread owns a pixel column for all
+// shots, so the in-place sweep needs no synchronisation.
+template <int RMAX>
+__global__ void __launch_bounds__(kThreads, 2)
+tikhonov_iter_kernel(float *__restrict__ u, float *__restrict__ d, const float *__restrict__ b,
+                     const uint32_t *__restrict__ words, int wstride, int HW, int R, int N,
+                     float rho, float lam, float gam, float *__restrict__ v_out,
+                     float *__restrict__ vprev, double *__restrict__ partials)
+{
+    const int p = blockIdx.x * kThreads + threadIdx.x;
+    const int Z = N * R;
+    const float den = 2.f * lam + rho + 2.f * gam;
+    double sdv = 0.0, sv = 0.0;
+    if (p < HW) {
+        float prev = gam > 0.f ? u[(Z - 1) * HW + p] : 0.f;  // u_{Z-1}, not yet updated
+        float first_new = 0.f;
+        for (int j = 0; j < N; ++j) {
+            const uint32_t word = words[j * wstride + p];
+            const int base = j * R * HW + p;
+            float ur[RMAX], dr[RMAX];
+            float s = 0.f;
+#pragma unroll
+            for (int r = 0; r < RMAX; ++r) {
+                if (r < R) {
+                    ur[r] = u[base + r * HW];
+                    dr[r] = d[base + r * HW];
+                    if (bit(word, r)) s += ur[r] - dr[r];
+                }
+            }
+            const float e = (b[j * HW + p] - s) / (rho + (float)__popc(word));
+#pragma unroll
+            for (int r = 0; r < RMAX; ++r) {
+                if (r < R) {
+                    const int n = j * R + r;
+                    const int o = base + r * HW;
+                    const float g = ur[r] - dr[r];
+                    const float v = bit(word, r) ? g + e : g;
+                    const float w = v + dr[r];
+                    float un;
+                    if (gam > 0.f) {
+                        float next;
+                        if (n == Z - 1) next = first_new;
+                        else if (r + 1 < R) next = ur[r + 1 < RMAX ? r + 1 : r];
+                        else next = u[o + HW];  // first plane of the next shot, still old
+                        un = (rho * w + gam * (prev + next)) / den;
+                        prev = un;
+                        if (n == 0) first_new = un;
+                    } else {
+                        un = rho * w / den;
+                    }
+                    u[o] = un;
+                    d[o] = w - un;
+                    if (v_out) v_out[o] = v;
+                    if (vprev) {
+                        const double vp = vprev[o];
+                        sdv += ((double)v - vp) * ((double)v - vp);
+                        sv += vp * vp;
+                        vprev[o] = v;
+                    }
+                }
+            }
+        }
+    }
+    if (partials) {
+        block_sum2(sdv, sv);
+        if (threadIdx.x == 0) partials[2 * blockIdx.x] = sdv, partials[2 * blockIdx.x + 1] = sv;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) tikhonov_prox_kernel(const float *__restrict__ in,
+                                                                 float *__restrict__ out,
+                                                                 long long n, float rho,
+                                                                 float lam)
+{
+    const float den = 2.f * lam + rho;
+    for (long long i = blockIdx.x * (long long)kThreads + threadIdx.x; i < n;
+         i += (long long)gridDim.x * kThreads)
+        out[i] = rho * in[i] / den;
+}
+
+// PSNR partials: per block max(ref) and sum (x - ref)^2 over a grid-stride range.
+__global__ void __launch_bounds__(kThreads) psnr_partials_kernel(const float *__restrict__ x,
+                                                                 const float *__restrict__ ref,
+                                                                 size_t n,
+                                                                 double *__restrict__ partials)
+{
+    double e = 0.0, mx = -INFINITY;
+    for (size_t i = blockIdx.x * (size_t)kThreads + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * kThreads) {
+        const float r = ref[i];
+        const double t = (double)x[i] - (double)r;
+        e += t * t;
+        mx = fmax(mx, (double)r);
+    }
+    __shared__ double se[kThreads / 32], sm[kThreads / 32];
+    for (int o = 16; o > 0; o >>= 1) {
+        e += __shfl_down_sync(0xffffffffu, e, o);
+        mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) { se[wid] = e; sm[wid] = mx; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, m = -INFINITY;
+        for (int k = 0; k < kThreads / 32; ++k) { a += se[k]; m = fmax(m, sm[k]); }
+        partials[2 * blockIdx.x] = a;
+        partials[2 * blockIdx.x + 1] = m;
+    }
+}
+
+// Sums `nblocks` pairs in a fixed order (one block): out = {sum a, sum c} or,
+// for PSNR, {sum e, max m} -> 10 log10(n V^2 / e).
+template <bool kPsnr>
+__global__ void __launch_bounds__(kThreads) finish_pairs_kernel(const double *__restrict__ partials,
+                                                                int nblocks, size_t n,
+                                                                double *__restrict__ out)
+{
+    double a = 0.0, c = kPsnr ? -INFINITY : 0.0;
+    for (int k = threadIdx.x; k < nblocks; k += kThreads) {
+        a += partials[2 * k];
+        c = kPsnr ? fmax(c, partials[2 * k + 1]) : c + partials[2 * k + 1];
+    }
+    __shared__ double sa[kThreads], sc[kThreads];
+    sa[threadIdx.x] = a;
+    sc[threadIdx.x] = c;
+    __syncthreads();
+    for (int s = kThreads / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            sa[threadIdx.x] += sa[threadIdx.x + s];
+            sc[threadIdx.x] = kPsnr ? fmax(sc[threadIdx.x], sc[threadIdx.x + s])
+                                    : sc[threadIdx.x] + sc[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        if (kPsnr) {
+            out[0] = 10.0 * log10((double)n * sc[0] * sc[0] / sa[0]);
+        } else {
+            out[0] = sa[0];
+            out[1] = sc[0];
+        }
+    }
+}
+
+inline dim3 pixel_grid(int HW, int ny) { return dim3((HW + kThreads - 1) / kThreads, ny); }
+
+}  // namespace
+
+int reduction_blocks() { return kRedBlocks; }
+
+cslsm_status launch_pack_masks(const uint8_t *masks, uint32_t *words, int HW, int R, int nsets,
+                               cudaStream_t s)
+{
+    LaunchScope ls(K_PACK, s);
+    pack_masks_kernel<<<pixel_grid(HW, nsets), kThreads, 0, s>>>(masks, words, HW, R);
+    CSLSM_LAUNCHED();
+    return CSLSM_OK;
+}
+
+cslsm_status launch_forward(const Geom &g, Masks m, const float *v, float *b, cudaStream_t s)
+{
+    LaunchScope ls(K_FORWARD, s);
+    forward_kernel<<<pixel_grid(g.HW(), g.N), kThreads, 0, s>>>(v, b, m.words, m.wstride, g.HW(),
+                                                                g.R);
+    CSLSM_LAUNCHED();
+    return CSLSM_OK;
+}
+
+cslsm_status launch_adjoint(const Geom &g, Masks m, const float *b, float *v, cudaStream_t s)
+{
+    LaunchScope ls(K_ADJOINT, s);
+    adjoint_kernel<<<pixel_grid(g.HW(), g.N), kThreads, 0, s>>>(b, v, m.words, m.wstride, g.HW(),
+                                                                g.R);
+    CSLSM_LAUNCHED();
+    return CSLSM_OK;
+}
+
+cslsm_status launch_xupdate_w(const Geom &g, Masks m, const float *u, const float *d,
+                              const float *b, float rho, float *w, float *v_out, float *vprev,
+                              double *partials, int nblocks_red, cudaStream_t s)
+{
+    const dim3 grid = pixel_grid(g.HW(), g.N);
+    if (partials && (int)(grid.x * grid.y) > nblocks_red) {
+        set_error("reduction buffer too small");
+        return CSLSM_ERR_INVALID_ARG;
+    }
+#define XU(RM)                                                                                \
+    xupdate_w_kernel<RM><<<grid, kThreads, 0, s>>>(u, d, b, m.words, m.wstride, g.HW(), g.R, \
+                                                   rho, w, v_out, vprev, partials)
+    LaunchScope ls(K_XUPDATE, s);
+    if (g.R <= 4) XU(4);
+    else if (g.R <= 8) XU(8);
+    else if (g.R <= 16) XU(16);
+    else XU(32);
+#undef XU
+    CSLSM_LAUNCHED();
+    return CSLSM_OK;
+}
+
+cslsm_status launch_tikhonov_iter(const Geom &g, Masks m, float *u, float *d, const float *b,
+                                  float rho, float lam, float gam, float *v_out, float *vprev,
+                                  double *partials, int nblocks_red, cudaStream_t s)
+{
+    const dim3 grid = pixel_grid(g.HW(), 1);
+    if (partials && (int)grid.x > nblocks_red) {
+        set_error("reduction buffer too small");
+        return CSLSM_ERR_INVALID_ARG;
+    }
+#define TK(RM)                                                                                 \
+    tikhonov_iter_kernel<RM><<<grid, kThreads, 0, s>>>(u, d, b, m.words, m.wstride, g.HW(), g.R, \
+                                                       g.N, rho, lam, gam, v_out, vprev, partials)
+    LaunchScope ls(K_TIK_ITER, s);
+    if (g.R <= 4) TK(4);
+    else if (g.R <= 8) TK(8);
+    else if (g.R <= 16) TK(16);
+    else TK(32);
+#undef TK
+    CSLSM_LAUNCHED();
+    return CSLSM_OK;
+}
+
+cslsm_status launch_tikhonov_prox(const float *in, float *out, long long n, float rho, float lam,
+                                  cudaStream_t s)
+{
+    long long blocks = (n + kThreads - 1) / kThreads;
+    if (blocks > 8192) blocks = 8192;
+    if (blocks < 1) blocks = 1;
+    LaunchScope ls(K_TIK_PROX, s);
+    tikhonov_prox_kernel<<<(unsigned)blocks, kThreads, 0, s>>>(in, out, n, rho, lam);
+    CSLSM_LAUNCHED();
+    return CSLSM_OK;
+}
+
+cslsm_status launch_psnr_partials(const float *x, const float *ref, size_t n, double *partials,
+                                  int nblocks, cudaStream_t s)
+{
+    LaunchScope ls(K_PSNR, s);
+    psnr_partials_kernel<<<nblocks, kThreads, 0, s>>>(x, ref, n, partials);
+    CSLSM_LAUNCHED();
+    return CSLSM_OK;
+}
+
+cslsm_status launch_psnr_finish(const double *partials, int nblocks, size_t n, double *out,
+                                cudaStream_t s)
+{
+    LaunchScope ls(K_REDUCE, s);
+    finish_pairs_kernel<true><<<1, kThreads, 0, s>>>(partials, nblocks, n, out);
+    CSLSM_LAUNCHED();
+    return CSLSM_OK;
+}
+
+cslsm_status launch_sum_pairs(const double *partials, int nblocks, double *out2, cudaStream_t s)
+{
+    LaunchScope ls(K_REDUCE, s);
+    finish_pairs_kernel<false><<<1, kThreads, 0, s>>>(partials, nblocks, 0, out2);
+    CSLSM_LAUNCHED();
+    return CSLSM_OK;
+}
+
+}  // namespace cslsm
