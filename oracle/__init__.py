@@ -65,6 +65,18 @@ def lib() -> ctypes.CDLL:
         L.or_psnr.restype = d
         L.or_bm3d.argtypes = [i, i, P, d, P]
         L.or_bm3d.restype = i
+        L.or_bm3d_stage.argtypes = [i, i, P, P, d, d, P]
+        L.or_bm3d_stage.restype = i
+        L.or_bm3d_match.argtypes = [i, i, P, i, P, P]
+        L.or_bm3d_match.restype = i
+        L.or_bm3d_ref_positions.argtypes = [i, P]
+        L.or_bm3d_ref_positions.restype = i
+        L.or_bm3d_dct8.argtypes = [P]
+        L.or_bm3d_dct8.restype = None
+        L.or_bm3d_transform.argtypes = [i, P, i]
+        L.or_bm3d_transform.restype = None
+        L.or_bm3d_kaiser.argtypes = [P]
+        L.or_bm3d_kaiser.restype = None
         L.or_admm.argtypes = [i, i, i, i, P, i, P, d, d, d, i, d, i, i, d, d, i, P, P, P,
                               ctypes.POINTER(ctypes.c_int)]
         L.or_admm.restype = i
@@ -164,6 +176,56 @@ def bm3d(g, sigma: float) -> np.ndarray:
             raise RuntimeError(f"or_bm3d failed ({rc})")
         out[z] = oz
     return out[0] if squeeze else out
+
+
+def bm3d_stage(noisy, sigma: float, guide=None, lambda3d: float = 2.7) -> np.ndarray:
+    """One BM3D stage on one slice [H,W]: hard threshold (guide None) or Wiener."""
+    noisy = _f64(noisy)
+    H, W = noisy.shape
+    out = np.empty_like(noisy)
+    g = _f64(guide) if guide is not None else None
+    rc = lib().or_bm3d_stage(H, W, _p(noisy), _p(g) if g is not None else None, float(sigma),
+                             float(lambda3d), _p(out))
+    if rc != 0:
+        raise RuntimeError(f"or_bm3d_stage failed ({rc})")
+    return out
+
+
+def bm3d_ref_positions(n: int) -> list[int]:
+    buf = np.zeros(n + 2, dtype=np.int32)
+    k = lib().or_bm3d_ref_positions(int(n), _p(buf))
+    return buf[:k].tolist()
+
+
+def bm3d_match(img, stage: int):
+    """Match lists of one slice: (idx [nref,16] int64 with -1 padding, counts [nref])."""
+    img = _f64(img)
+    H, W = img.shape
+    nref = max(1, len(bm3d_ref_positions(H)) * len(bm3d_ref_positions(W)))
+    idx = np.full((nref, 16), -1, dtype=np.int64)
+    cnt = np.zeros(nref, dtype=np.int32)
+    k = lib().or_bm3d_match(H, W, _p(img), int(stage), _p(idx), _p(cnt))
+    if k < 0:
+        raise MemoryError("or_bm3d_match failed")
+    return idx[:k], cnt[:k]
+
+
+def bm3d_dct8() -> np.ndarray:
+    C = np.empty((8, 8))
+    lib().or_bm3d_dct8(_p(C))
+    return C
+
+
+def bm3d_transform(group, inverse: bool = False) -> np.ndarray:
+    g = _f64(group).copy()
+    lib().or_bm3d_transform(g.shape[0], _p(g), int(bool(inverse)))
+    return g
+
+
+def bm3d_kaiser() -> np.ndarray:
+    K = np.empty((8, 8))
+    lib().or_bm3d_kaiser(_p(K))
+    return K
 
 
 def psnr(x, ref) -> float:
