@@ -36,7 +36,7 @@ extern "C" {
 #endif
 
 #define CSLSM_MAX_R 32
-#define CSLSM_ABI_VERSION 1
+#define CSLSM_ABI_VERSION 2
 
 typedef enum {
     CSLSM_OK = 0,
@@ -54,6 +54,15 @@ typedef enum {
     CSLSM_DEN_BM3D = 2      /* block matching + 3D collaborative filtering */
 } cslsm_denoiser;
 
+/* Element type of the ADMM state u, d and of the plan's w = v + d workspace
+ * (arithmetic is always FP32; the x-update division by rho + diag(Phi Phi^T),
+ * the residuals and v_out stay FP32). */
+typedef enum {
+    CSLSM_STORE_FP32 = 0,
+    CSLSM_STORE_BF16 = 1, /* bfloat16, round to nearest even on store */
+    CSLSM_STORE_FP16 = 2  /* IEEE half, round to nearest even on store */
+} cslsm_storage;
+
 /* Parameters of Algorithm 1 and of its denoiser.
  *   rho     > 0   ADMM penalty (augmented Lagrangian of Sec. III-B).
  *   lambda  >= 0  prior weight (Eq. model-slice).  Ignored by BM3D, whose
@@ -70,7 +79,9 @@ typedef enum {
  *   tv_tau        TV: dual step, 0 < tv_tau <= 0.25 (1/8 is the convergent
  *                 bound of Chambolle 2004).
  *   bm3d_sigma    BM3D: noise standard deviation on the volume's scale (> 0).
- *   init_user     0: u^0 = d^0 = 0.  1: u_io / d_io hold u^0, d^0. */
+ *   init_user     0: u^0 = d^0 = 0.  1: u_io / d_io hold u^0, d^0.
+ *   storage       a cslsm_storage: element type of u_io / d_io and of the
+ *                 plan's state and workspace. */
 typedef struct {
     float rho;
     float lambda;
@@ -83,6 +94,7 @@ typedef struct {
     float tv_tau;
     float bm3d_sigma;
     int init_user;
+    int storage;
 } cslsm_admm_params;
 
 /* Filled by cslsm_admm_solve when non-NULL (host memory). */
@@ -126,24 +138,55 @@ cslsm_status cslsm_adjoint(cslsm_plan plan, const float *b, float *v, void *stre
  * dual update d <- d + v - u (Eq. ADMM).
  *   b       device [n_shots][H][W] measurement.
  *   v_out   device [Z][H][W]: receives v^K, Algorithm 1's output.
- *   u_io, d_io  device [Z][H][W] or NULL.  When given they are the ADMM
- *           state (read as u^0, d^0 if init_user, always written with u^K,
- *           d^K), which lets a caller resume a solve; when NULL the plan's
- *           own state buffers are used (then init_user must be 0).
+ *   u_io, d_io  device [Z][H][W] arrays of params->storage elements, or
+ *           NULL.  When given they are the ADMM state (read as u^0, d^0 if
+ *           init_user, always written with u^K, d^K), which lets a caller
+ *           resume a solve; when NULL the plan's own state buffers are used
+ *           (then init_user must be 0).
  *   stats   host, optional.
  * v_out must not overlap u_io, d_io or b. */
 cslsm_status cslsm_admm_solve(cslsm_plan plan, const float *b, const cslsm_admm_params *params,
-                              float *v_out, float *u_io, float *d_io, cslsm_admm_stats *stats,
+                              float *v_out, void *u_io, void *d_io, cslsm_admm_stats *stats,
                               void *stream);
 
 /* The u-step denoiser alone, slice by slice, without z coupling (Eq. u-sub):
  *   Tikhonov: out = rho * in / (2 lambda + rho);
  *   TV:       out = argmin theta*TV(u) + 1/2||u - in||^2, theta = lambda / rho,
  *             by params->tv_inner Chambolle steps from p = 0;
- *   BM3D:     out = BM3D(in) at noise level params->bm3d_sigma.
+ *   BM3D:     out = BM3D(in) at noise level params->bm3d_sigma (stage 1 then
+ *             stage 2, see cslsm_bm3d_stage; scratch from cudaMallocAsync).
  * in, out: device [Z][H][W]; they must not overlap (neighbour reads). */
 cslsm_status cslsm_denoise(int denoiser, const float *in, float *out, int Z, int H, int W,
                            const cslsm_admm_params *params, void *stream);
+
+/* ---- BM3D stages (the u-step denoiser of Sec. III-B / IV-C, by stage) ------
+ * The variant built here, applied to each 2-D slice: 8 x 8 patches, reference
+ * patches every 3 pixels plus the last position, a 39 x 39 search window,
+ * matching on the 8-bit codes clamp(rint(x * 255), 0, 255) by exact integer
+ * SSD with thresholds 64 * 2500 (stage 1) and 64 * 400 (stage 2), groups of
+ * the reference plus up to 15 others in (SSD, y * W + x) order cut to a power
+ * of two, an orthonormal 8 x 8 DCT-II + Haar group transform, hard threshold
+ * 2.7 sigma (stage 1) or Wiener shrinkage guided by the basic estimate
+ * (stage 2), and Kaiser-window (beta = 2) weighted aggregation.  Slices
+ * smaller than 8 x 8 are returned unchanged.  These calls allocate their
+ * scratch with cudaMallocAsync on `stream`. */
+
+/* Reference patches of one H x W slice (0 if H < 8 or W < 8). */
+int cslsm_bm3d_num_refs(int H, int W);
+
+/* Block matching of stage 1 or 2 on each slice of img (device [Z][H][W]):
+ * lists (device int32 [Z][nref][16]) receives, per reference in row-major
+ * order of the reference grid, the patch positions y * W + x of its group
+ * (reference first, -1 padding); counts (device int32 [Z][nref]) the group
+ * sizes before the power-of-two cut.  Needs H, W >= 8. */
+cslsm_status cslsm_bm3d_match(const float *img, int Z, int H, int W, int stage, int *lists,
+                              int *counts, void *stream);
+
+/* One BM3D stage on every slice: stage 1 (hard threshold) of noisy, or
+ * stage 2 (Wiener) of noisy guided by the basic estimate `guide` (device
+ * [Z][H][W], matched on).  out: device [Z][H][W], not overlapping the inputs. */
+cslsm_status cslsm_bm3d_stage(int stage, const float *noisy, const float *guide, float *out,
+                              int Z, int H, int W, float sigma, void *stream);
 
 /* Volume PSNR of Sec. IV (all voxels as one array): writes
  * 10 log10(n V^2 / ||x - ref||^2), V = max(ref), as a double to out (device).
@@ -158,6 +201,22 @@ const char *cslsm_last_error(void);
 
 /* CSLSM_ABI_VERSION of the loaded library. */
 int cslsm_abi_version(void);
+
+/* TV prox tile shapes (process-wide setting).  The TV kernel comes in four
+ * variants (column chunks x row bands) with a tile shape chosen per launch
+ * geometry.  mode 0 (default): shapes from a cost model of the work per SM.
+ * mode 1: on the first launch of each (device, H, W, steps, slices) key that
+ * is not being captured into a CUDA graph, time every variant on the actual
+ * launch (three runs each; the prox is idempotent, so this only costs time)
+ * with a synchronisation of the stream, and keep the fastest for later
+ * launches.  modes 2..5: force variant mode - 2 (for tests).  Changing the
+ * mode clears the kept choices. */
+cslsm_status cslsm_set_autotune(int mode);
+
+/* The TV tile shape a prox launch of this geometry would use now (on the
+ * current device): shape4 (host int[4]) = {variant, tile rows, tile columns,
+ * region rows}.  steps <= 24 (longer proxes run in chunks). */
+cslsm_status cslsm_tv_shape(int H, int W, int steps, int nslices, int *shape4);
 
 /* ---- instrumentation (benchmarks, tracing) ------------------------------ */
 

@@ -23,6 +23,8 @@ LIB_PATH = os.path.join(_HERE, "libcslsm.so")
 TIKHONOV, TV, BM3D = 0, 1, 2
 DENOISERS = {"tikhonov": TIKHONOV, "tv": TV, "bm3d": BM3D}
 MAX_R = 32
+STORAGE = {"fp32": 0, "bf16": 1, "fp16": 2}
+STORAGE_DTYPE = {"fp32": torch.float32, "bf16": torch.bfloat16, "fp16": torch.float16}
 
 STATUS = {0: "CSLSM_OK", 1: "CSLSM_ERR_INVALID_ARG", 2: "CSLSM_ERR_CUDA",
           3: "CSLSM_ERR_TIMEOUT", 4: "CSLSM_ERR_UNSUPPORTED", 5: "CSLSM_ERR_OOM"}
@@ -41,7 +43,8 @@ class AdmmParams(ctypes.Structure):
                 ("gamma", ctypes.c_float), ("iters", ctypes.c_int), ("tol", ctypes.c_float),
                 ("check_every", ctypes.c_int), ("denoiser", ctypes.c_int),
                 ("tv_inner", ctypes.c_int), ("tv_tau", ctypes.c_float),
-                ("bm3d_sigma", ctypes.c_float), ("init_user", ctypes.c_int)]
+                ("bm3d_sigma", ctypes.c_float), ("init_user", ctypes.c_int),
+                ("storage", ctypes.c_int)]
 
 
 class AdmmStats(ctypes.Structure):
@@ -62,12 +65,13 @@ class Params:
     tv_inner: int = 20
     tv_tau: float = 0.125
     bm3d_sigma: float = 0.05
+    storage: str = "fp32"
 
     def to_c(self, init_user: bool = False) -> AdmmParams:
         return AdmmParams(float(self.rho), float(self.lam), float(self.gamma), int(self.iters),
                           float(self.tol), int(self.check_every), DENOISERS[self.denoiser],
                           int(self.tv_inner), float(self.tv_tau), float(self.bm3d_sigma),
-                          int(bool(init_user)))
+                          int(bool(init_user)), STORAGE[self.storage])
 
 
 _lib = None
@@ -93,6 +97,8 @@ def lib() -> ctypes.CDLL:
                              ctypes.POINTER(AdmmStats), P],
         "cslsm_denoise": [I, P, P, I, I, I, ctypes.POINTER(AdmmParams), P],
         "cslsm_psnr": [P, P, ctypes.c_size_t, P, P],
+        "cslsm_bm3d_match": [P, I, I, I, I, P, P, P],
+        "cslsm_bm3d_stage": [I, P, P, P, I, I, I, F, P],
     }
     for name, args in sigs.items():
         fn = getattr(L, name)
@@ -104,6 +110,12 @@ def lib() -> ctypes.CDLL:
     L.cslsm_last_error.restype = ctypes.c_char_p
     L.cslsm_abi_version.argtypes = []
     L.cslsm_abi_version.restype = I
+    L.cslsm_tv_shape.argtypes = [I, I, I, I, P]
+    L.cslsm_tv_shape.restype = I
+    L.cslsm_set_autotune.argtypes = [I]
+    L.cslsm_set_autotune.restype = I
+    L.cslsm_bm3d_num_refs.argtypes = [I, I]
+    L.cslsm_bm3d_num_refs.restype = I
     L.cslsm_launch_count.argtypes = []
     L.cslsm_launch_count.restype = ctypes.c_ulonglong
     L.cslsm_timing_enable.argtypes = [I]
@@ -185,11 +197,13 @@ class Plan:
     def solve(self, b: torch.Tensor, params: Params, v_out: torch.Tensor | None = None,
               u: torch.Tensor | None = None, d: torch.Tensor | None = None,
               init_user: bool = False, stream=None, stats: bool = False):
-        """Algorithm 1; returns v^K (and the cslsm_admm_stats fields if stats)."""
+        """Algorithm 1; returns v^K (and the cslsm_admm_stats fields if stats).
+        u, d (optional state) have the dtype of params.storage."""
         if v_out is None:
             v_out = torch.empty(self.vol_shape, dtype=torch.float32, device=b.device)
-        up = _dev(u, "u", torch.float32, self.vol_shape) if u is not None else None
-        dp = _dev(d, "d", torch.float32, self.vol_shape) if d is not None else None
+        sd = STORAGE_DTYPE[params.storage]
+        up = _dev(u, "u", sd, self.vol_shape) if u is not None else None
+        dp = _dev(d, "d", sd, self.vol_shape) if d is not None else None
         st = AdmmStats()
         cp = params.to_c(init_user)
         _check(lib().cslsm_admm_solve(self._h, _dev(b, "b", torch.float32, self.meas_shape),
@@ -255,3 +269,48 @@ def timing_read(kernel: str, reset: bool = False) -> tuple[int, float]:
     _check(lib().cslsm_timing_read(kernel.encode(), ctypes.byref(n), ctypes.byref(ms),
                                    int(bool(reset))), "cslsm_timing_read")
     return int(n.value), float(ms.value)
+
+
+def bm3d_match(img: torch.Tensor, stage: int, stream=None):
+    """Block-matching groups of every reference of each slice of img [Z,H,W]:
+    (lists int32 [Z,nref,16] of y*W+x positions, counts int32 [Z,nref])."""
+    if img.dim() == 2:
+        img = img[None]
+    Z, H, W = img.shape
+    nref = int(lib().cslsm_bm3d_num_refs(H, W))
+    lists = torch.empty((Z, nref, 16), dtype=torch.int32, device=img.device)
+    counts = torch.empty((Z, nref), dtype=torch.int32, device=img.device)
+    _check(lib().cslsm_bm3d_match(_dev(img, "img", torch.float32), Z, H, W, int(stage),
+                                  ctypes.c_void_p(lists.data_ptr()),
+                                  ctypes.c_void_p(counts.data_ptr()), _stream(stream)),
+           "cslsm_bm3d_match")
+    return lists, counts
+
+
+def bm3d_stage(stage: int, noisy: torch.Tensor, sigma: float, guide: torch.Tensor | None = None,
+               out: torch.Tensor | None = None, stream=None):
+    """One BM3D stage on each slice: 1 = hard threshold, 2 = Wiener guided by `guide`."""
+    if noisy.dim() == 2:
+        noisy = noisy[None]
+        guide = guide[None] if guide is not None else None
+    Z, H, W = noisy.shape
+    if out is None:
+        out = torch.empty_like(noisy)
+    gp = _dev(guide, "guide", torch.float32, (Z, H, W)) if guide is not None else None
+    _check(lib().cslsm_bm3d_stage(int(stage), _dev(noisy, "noisy", torch.float32), gp,
+                                  _dev(out, "out", torch.float32, (Z, H, W)), Z, H, W,
+                                  float(sigma), _stream(stream)), "cslsm_bm3d_stage")
+    return out
+
+
+def set_autotune(mode: int) -> None:
+    """TV tile shapes: 0 cost model, 1 timed autotuning, 2..5 force a variant."""
+    _check(lib().cslsm_set_autotune(int(mode)), "cslsm_set_autotune")
+
+
+def tv_shape(H: int, W: int, steps: int, nslices: int) -> dict:
+    """The TV kernel variant and tile shape a launch of this geometry uses now."""
+    buf = (ctypes.c_int * 4)()
+    _check(lib().cslsm_tv_shape(int(H), int(W), int(steps), int(nslices), buf),
+           "cslsm_tv_shape")
+    return {"variant": buf[0], "tile_rows": buf[1], "tile_cols": buf[2], "region_rows": buf[3]}

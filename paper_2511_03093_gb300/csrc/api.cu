@@ -42,6 +42,8 @@ struct cslsm_plan_s {
     double *partials = nullptr;  // reduction partials (2 doubles per block)
     int npartials = 0;
     double *red_out = nullptr;  // 2 doubles
+    void *bm3d_ws = nullptr;     // BM3D workspace (zero-filled on allocation)
+    size_t bm3d_ws_bytes = 0;
 };
 
 namespace {
@@ -88,6 +90,8 @@ cslsm_status check_params(const cslsm_admm_params *p, bool for_denoise)
     CHECK_ARG(finite_f(p->tol) && p->tol >= 0.f, "tol must be finite and >= 0");
     if (p->tol > 0.f) CHECK_ARG(p->check_every >= 1, "check_every must be >= 1 when tol > 0");
     CHECK_ARG(p->init_user == 0 || p->init_user == 1, "init_user must be 0 or 1");
+    CHECK_ARG(p->storage >= CSLSM_STORE_FP32 && p->storage <= CSLSM_STORE_FP16,
+              "unknown storage type %d", p->storage);
     return CSLSM_OK;
 }
 
@@ -112,6 +116,7 @@ void free_plan(cslsm_plan_s *p)
     cudaFree(p->pbuf);
     cudaFree(p->partials);
     cudaFree(p->red_out);
+    cudaFree(p->bm3d_ws);
     delete p;
 }
 
@@ -241,7 +246,7 @@ cslsm_status cslsm_adjoint(cslsm_plan plan, const float *b, float *v, void *stre
 }
 
 cslsm_status cslsm_admm_solve(cslsm_plan plan, const float *b, const cslsm_admm_params *prm,
-                              float *v_out, float *u_io, float *d_io, cslsm_admm_stats *stats,
+                              float *v_out, void *u_io, void *d_io, cslsm_admm_stats *stats,
                               void *stream)
 {
     CHECK_ARG(plan != nullptr, "plan is NULL");
@@ -250,23 +255,21 @@ cslsm_status cslsm_admm_solve(cslsm_plan plan, const float *b, const cslsm_admm_
     if (st) return st;
     CHECK_ARG((u_io == nullptr) == (d_io == nullptr), "give both u_io and d_io or neither");
     CHECK_ARG(!prm->init_user || u_io != nullptr, "init_user needs u_io and d_io");
-    if (prm->denoiser == CSLSM_DEN_BM3D) {
-        set_error("BM3D denoiser is not built in this library");
-        return CSLSM_ERR_UNSUPPORTED;
-    }
     st = check_device(plan);
     if (st) return st;
 
     const Geom &g = plan->g;
     const size_t nv = (size_t)g.voxels();
     cudaStream_t s = as_stream(stream);
-    float *u = u_io ? u_io : plan->u;
-    float *d = d_io ? d_io : plan->d;
+    void *u = u_io ? u_io : (void *)plan->u;
+    void *d = d_io ? d_io : (void *)plan->d;
+    const int store = prm->storage;
+    const size_t esz = store == CSLSM_STORE_FP32 ? 4 : 2;
     const float gam = g.Z() > 1 ? prm->gamma : 0.f;
     const bool use_tol = prm->tol > 0.f;
     if (!prm->init_user) {
-        CSLSM_CUDA(cudaMemsetAsync(u, 0, sizeof(float) * nv, s));
-        CSLSM_CUDA(cudaMemsetAsync(d, 0, sizeof(float) * nv, s));
+        CSLSM_CUDA(cudaMemsetAsync(u, 0, esz * nv, s));
+        CSLSM_CUDA(cudaMemsetAsync(d, 0, esz * nv, s));
     }
     if (use_tol) {
         if (!plan->vprev) CSLSM_CUDA(cudaMalloc(&plan->vprev, sizeof(float) * nv));
@@ -284,6 +287,18 @@ cslsm_status cslsm_admm_solve(cslsm_plan plan, const float *b, const cslsm_admm_
             plan->pbuf_floats = need;
         }
     }
+    if (prm->denoiser == CSLSM_DEN_BM3D) {
+        const size_t need = bm3d_workspace_bytes(gam > 0.f ? 1 : g.Z(), g.H, g.W);
+        if (plan->bm3d_ws_bytes < need) {
+            CSLSM_CUDA(cudaStreamSynchronize(s));
+            cudaFree(plan->bm3d_ws);
+            plan->bm3d_ws = nullptr;
+            plan->bm3d_ws_bytes = 0;
+            CSLSM_CUDA(cudaMalloc(&plan->bm3d_ws, need));
+            CSLSM_CUDA(cudaMemsetAsync(plan->bm3d_ws, 0, need, s));
+            plan->bm3d_ws_bytes = need;
+        }
+    }
     const Masks m = masks_of(plan);
     int k = 0;
     double rel = -1.0;
@@ -295,14 +310,44 @@ cslsm_status cslsm_admm_solve(cslsm_plan plan, const float *b, const cslsm_admm_
         float *vp = use_tol ? plan->vprev : nullptr;
         double *part = check ? plan->partials : nullptr;
         if (prm->denoiser == CSLSM_DEN_TIKHONOV) {
-            st = launch_tikhonov_iter(g, m, u, d, b, prm->rho, prm->lambda, gam, vo, vp, part,
-                                      plan->npartials, s);
+            st = launch_tikhonov_iter(g, m, store, u, d, b, prm->rho, prm->lambda, gam, vo, vp,
+                                      part, plan->npartials, s);
             if (st) return st;
+        } else if (prm->denoiser == CSLSM_DEN_BM3D) {
+            st = launch_xupdate_w(g, m, store, u, d, b, prm->rho, plan->w, vo, vp, part,
+                                  plan->npartials, s);
+            if (st) return st;
+            Bm3dSlices a{};
+            a.storage = store;
+            a.src = plan->w;
+            a.u = u;
+            a.out = u;
+            a.dual = d;
+            a.Z = g.Z();
+            a.H = g.H;
+            a.W = g.W;
+            a.rho = prm->rho;
+            a.gamma = gam;
+            a.sigma = prm->bm3d_sigma;
+            if (gam == 0.f) {
+                a.n0 = 0;
+                a.nslices = g.Z();
+                st = bm3d_slices(a, plan->bm3d_ws, s);
+                if (st) return st;
+            } else {
+                a.nslices = 1;
+                for (int n = 0; n < g.Z(); ++n) {
+                    a.n0 = n;
+                    st = bm3d_slices(a, plan->bm3d_ws, s);
+                    if (st) return st;
+                }
+            }
         } else {
-            st = launch_xupdate_w(g, m, u, d, b, prm->rho, plan->w, vo, vp, part,
+            st = launch_xupdate_w(g, m, store, u, d, b, prm->rho, plan->w, vo, vp, part,
                                   plan->npartials, s);
             if (st) return st;
             TvSlices a{};
+            a.storage = store;
             a.w = plan->w;
             a.u = u;
             a.d = d;
@@ -376,10 +421,35 @@ cslsm_status cslsm_denoise(int denoiser, const float *in, float *out, int Z, int
     if (denoiser == CSLSM_DEN_TIKHONOV)
         return launch_tikhonov_prox(in, out, (long long)nv, prm->rho, prm->lambda, s);
     if (denoiser == CSLSM_DEN_BM3D) {
-        set_error("BM3D denoiser is not built in this library");
-        return CSLSM_ERR_UNSUPPORTED;
+        const size_t need = bm3d_workspace_bytes(Z, H, W);
+        void *ws = nullptr;
+        CSLSM_CUDA(cudaMallocAsync(&ws, need, s));
+        cudaError_t e = cudaMemsetAsync(ws, 0, need, s);
+        if (e != cudaSuccess) {
+            cudaFreeAsync(ws, s);
+            set_error("cudaMemsetAsync: %s", cudaGetErrorString(e));
+            return CSLSM_ERR_CUDA;
+        }
+        Bm3dSlices a{};
+        a.storage = CSLSM_STORE_FP32;
+        a.src = in;
+        a.u = nullptr;
+        a.out = out;
+        a.dual = nullptr;
+        a.Z = Z;
+        a.H = H;
+        a.W = W;
+        a.n0 = 0;
+        a.nslices = Z;
+        a.rho = 1.f;
+        a.gamma = 0.f;
+        a.sigma = prm->bm3d_sigma;
+        st = bm3d_slices(a, ws, s);
+        cudaFreeAsync(ws, s);
+        return st;
     }
     TvSlices a{};
+    a.storage = CSLSM_STORE_FP32;
     a.w = in;
     a.u = out;
     a.d = nullptr;
@@ -398,6 +468,66 @@ cslsm_status cslsm_denoise(int denoiser, const float *in, float *out, int Z, int
         CSLSM_CUDA(cudaMallocAsync(&pbuf, sizeof(float) * 4 * nv, s));
     st = tv_prox_slices(a, pbuf, s);
     if (pbuf) cudaFreeAsync(pbuf, s);
+    return st;
+}
+
+cslsm_status cslsm_set_autotune(int mode)
+{
+    CHECK_ARG(mode >= 0 && mode <= 5, "autotune mode must be in [0, 5]");
+    tv_set_mode(mode);
+    return CSLSM_OK;
+}
+
+cslsm_status cslsm_tv_shape(int H, int W, int steps, int nslices, int *shape4)
+{
+    CHECK_ARG(shape4 != nullptr, "shape4 is NULL");
+    CHECK_ARG(H >= 1 && W >= 1 && nslices >= 1, "H, W, nslices must be >= 1");
+    CHECK_ARG(steps >= 0 && steps <= tv_max_steps_per_launch(), "steps must be in [0, %d]",
+              tv_max_steps_per_launch());
+    return tv_query_shape(H, W, steps, nslices, shape4);
+}
+
+int cslsm_bm3d_num_refs(int H, int W) { return (H >= 1 && W >= 1) ? bm3d_nref(H, W) : 0; }
+
+cslsm_status cslsm_bm3d_match(const float *img, int Z, int H, int W, int stage, int *lists,
+                              int *counts, void *stream)
+{
+    CHECK_ARG(img != nullptr && lists != nullptr && counts != nullptr,
+              "img, lists and counts must be non-NULL");
+    CHECK_ARG(Z >= 1 && H >= 8 && W >= 8, "need Z >= 1 and H, W >= 8");
+    CHECK_ARG((long long)Z * H * W < (1ll << 31), "Z*H*W must be < 2^31");
+    CHECK_ARG(stage == 1 || stage == 2, "stage must be 1 or 2");
+    cudaStream_t s = as_stream(stream);
+    const size_t need = bm3d_workspace_bytes(Z, H, W);
+    void *ws = nullptr;
+    CSLSM_CUDA(cudaMallocAsync(&ws, need, s));
+    cslsm_status st = bm3d_match_only(img, Z, H, W, stage, lists, counts, ws, s);
+    cudaFreeAsync(ws, s);
+    return st;
+}
+
+cslsm_status cslsm_bm3d_stage(int stage, const float *noisy, const float *guide, float *out,
+                              int Z, int H, int W, float sigma, void *stream)
+{
+    CHECK_ARG(noisy != nullptr && out != nullptr, "noisy and out must be non-NULL");
+    CHECK_ARG(stage == 1 || (stage == 2 && guide != nullptr),
+              "stage must be 1, or 2 with a guide");
+    CHECK_ARG(Z >= 1 && H >= 1 && W >= 1, "Z, H, W must be >= 1");
+    CHECK_ARG((long long)Z * H * W < (1ll << 31), "Z*H*W must be < 2^31");
+    CHECK_ARG(std::isfinite(sigma) && sigma > 0.f, "sigma must be > 0");
+    cudaStream_t s = as_stream(stream);
+    const size_t need = bm3d_workspace_bytes(Z, H, W);
+    void *ws = nullptr;
+    CSLSM_CUDA(cudaMallocAsync(&ws, need, s));
+    cudaError_t e = cudaMemsetAsync(ws, 0, need, s);
+    cslsm_status st = CSLSM_OK;
+    if (e != cudaSuccess) {
+        set_error("cudaMemsetAsync: %s", cudaGetErrorString(e));
+        st = CSLSM_ERR_CUDA;
+    } else {
+        st = bm3d_stage_only(stage, noisy, guide, out, Z, H, W, sigma, ws, s);
+    }
+    cudaFreeAsync(ws, s);
     return st;
 }
 

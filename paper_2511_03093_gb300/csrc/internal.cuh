@@ -28,7 +28,7 @@ void set_error(const char *fmt, ...);
 // Kernels of the library, for launch accounting and sampled timing (timing.cu).
 enum KernelId {
     K_PACK = 0, K_FORWARD, K_ADJOINT, K_XUPDATE, K_TIK_ITER, K_TIK_PROX, K_TV_TILE, K_PSNR,
-    K_REDUCE, K_COUNT
+    K_REDUCE, K_BM3D_PREP, K_BM3D_MATCH, K_BM3D_FILTER, K_BM3D_FINISH, K_COUNT
 };
 
 // Wrap every kernel launch: counts it and, when timing is on, records CUDA
@@ -70,15 +70,16 @@ cslsm_status launch_adjoint(const Geom &g, Masks m, const float *b, float *v, cu
 // v^{k+1} to v_out.  When vprev != nullptr it also accumulates, per block,
 // sum (v^{k+1}-vprev)^2 and sum vprev^2 into partials[2*block] and then
 // stores v^{k+1} into vprev.
-cslsm_status launch_xupdate_w(const Geom &g, Masks m, const float *u, const float *d,
-                              const float *b, float rho, float *w, float *v_out, float *vprev,
+// u, d, w have the element type of `storage` (a cslsm_storage value).
+cslsm_status launch_xupdate_w(const Geom &g, Masks m, int storage, const void *u, const void *d,
+                              const float *b, float rho, void *w, float *v_out, float *vprev,
                               double *partials, int nblocks_red, cudaStream_t s);
 
 // One whole ADMM iteration with the Tikhonov prior fused into one pass:
 // v-update, Gauss-Seidel Tikhonov sweep along z (gamma > 0) and dual update.
-cslsm_status launch_tikhonov_iter(const Geom &g, Masks m, float *u, float *d, const float *b,
-                                  float rho, float lam, float gam, float *v_out, float *vprev,
-                                  double *partials, int nblocks_red, cudaStream_t s);
+cslsm_status launch_tikhonov_iter(const Geom &g, Masks m, int storage, void *u, void *d,
+                                  const float *b, float rho, float lam, float gam, float *v_out,
+                                  float *vprev, double *partials, int nblocks_red, cudaStream_t s);
 
 // Slice-wise Tikhonov prox out = rho*in/(2 lam + rho).
 cslsm_status launch_tikhonov_prox(const float *in, float *out, long long n, float rho, float lam,
@@ -95,9 +96,10 @@ cslsm_status launch_sum_pairs(const double *partials, int nblocks, double *out2,
 
 // ---- TV prox (kernels_tv.cu) ----------------------------------------------
 struct TvSlices {
-    const float *w;      // [Z][H][W] prox input source (w = v + d)
-    float *u;            // [Z][H][W] output u_n (and u_{n-1}, u_{n+1} source)
-    float *d;            // [Z][H][W] output d_n = w_n - u_n, or nullptr
+    int storage;         // element type of w, u, d (cslsm_storage)
+    const void *w;       // [Z][H][W] prox input source (w = v + d)
+    void *u;             // [Z][H][W] output u_n (and u_{n-1}, u_{n+1} source)
+    void *d;             // [Z][H][W] output d_n = w_n - u_n, or nullptr
     int H, W, Z;
     int n0, nslices;     // slices n0 .. n0+nslices-1
     float rho, gamma;    // g = (rho w + gamma (u_{n-1} + u_{n+1})) / (rho + 2 gamma)
@@ -110,5 +112,31 @@ struct TvSlices {
 // step count one launch covers; pbuf may be nullptr otherwise.
 cslsm_status tv_prox_slices(const TvSlices &a, float *pbuf, cudaStream_t s);
 int tv_max_steps_per_launch();
+// 0: tile shapes from the cost model; 1: time the kernel variants on the first
+// launch of every shape key (outside stream capture) and keep the fastest;
+// 2 + k: force variant k (tests).
+void tv_set_mode(int mode);
+// The shape (variant, TH, TW, RH) a launch of this geometry would use now.
+cslsm_status tv_query_shape(int H, int W, int T, int nslices, int *out4);
+
+// ---- BM3D (kernels_bm3d.cu) -------------------------------------------------
+struct Bm3dSlices {
+    int storage;       // element type of src, u, out, dual (cslsm_storage)
+    const void *src;   // [Z][H][W] u-step input source: w = v + d (ADMM) or the image
+    const void *u;     // [Z][H][W] z neighbours when gamma > 0
+    void *out;         // [Z][H][W] receives the denoised slices n0 .. n0+nslices-1
+    void *dual;        // [Z][H][W] receives src - out for those slices, or nullptr
+    int Z, H, W, n0, nslices;
+    float rho, gamma, sigma;
+};
+int bm3d_nref(int H, int W);
+// Device workspace for nslices slices; it must be zero-filled before its first
+// use (the accumulators are cleared again by every call).
+size_t bm3d_workspace_bytes(int nslices, int H, int W);
+cslsm_status bm3d_slices(const Bm3dSlices &b, void *ws, cudaStream_t s);
+cslsm_status bm3d_stage_only(int stage, const float *noisy, const float *guide, float *out,
+                             int nslices, int H, int W, float sigma, void *ws, cudaStream_t s);
+cslsm_status bm3d_match_only(const float *img, int nslices, int H, int W, int stage, int *lists,
+                             int *counts, void *ws, cudaStream_t s);
 
 }  // namespace cslsm

@@ -11,6 +11,7 @@
 #include <stdint.h>
 
 #include "internal.cuh"
+#include "storage.cuh"
 
 namespace cslsm {
 namespace {
@@ -91,11 +92,11 @@ __device__ __forceinline__ void block_sum2(double &a, double &c)
 // Woodbury x-update (Eq. v-update): for shot j at pixel p,
 //   g_r = u_r - d_r,  e = (b_j - sum_r phi_r g_r) / (rho + popc),
 //   v_r = g_r + phi_r e,  w_r = v_r + d_r.
-template <int RMAX>
+template <int RMAX, typename S>
 __global__ void __launch_bounds__(kThreads, 2)
-xupdate_w_kernel(const float *__restrict__ u, const float *__restrict__ d,
+xupdate_w_kernel(const S *__restrict__ u, const S *__restrict__ d,
                  const float *__restrict__ b, const uint32_t *__restrict__ words, int wstride,
-                 int HW, int R, float rho, float *__restrict__ w, float *__restrict__ v_out,
+                 int HW, int R, float rho, S *__restrict__ w, float *__restrict__ v_out,
                  float *__restrict__ vprev, double *__restrict__ partials)
 {
     const int p = blockIdx.x * kThreads + threadIdx.x;
@@ -109,8 +110,8 @@ xupdate_w_kernel(const float *__restrict__ u, const float *__restrict__ d,
 #pragma unroll
         for (int r = 0; r < RMAX; ++r) {
             if (r < R) {
-                dr[r] = __ldg(d + base + r * HW);
-                g[r] = __ldg(u + base + r * HW) - dr[r];
+                dr[r] = ld<S>(d + base + r * HW);
+                g[r] = ld<S>(u + base + r * HW) - dr[r];
                 if (bit(word, r)) s += g[r];
             }
         }
@@ -120,7 +121,7 @@ xupdate_w_kernel(const float *__restrict__ u, const float *__restrict__ d,
             if (r < R) {
                 const int o = base + r * HW;
                 const float v = bit(word, r) ? g[r] + e : g[r];
-                w[o] = v + dr[r];
+                st<S>(w + o, v + dr[r]);
                 if (v_out) v_out[o] = v;
                 if (vprev) {
                     const double vp = vprev[o];
@@ -147,9 +148,9 @@ xupdate_w_kernel(const float *__restrict__ u, const float *__restrict__ d,
 //   u_n = (rho w_n + gam (u_{n-1} + u_{n+1})) / (2 lam + rho + 2 gam),
 // and d_n = w_n - u_n  (= d + v - u).  One thread owns a pixel column for all
 // shots, so the in-place sweep needs no synchronisation.
-template <int RMAX>
+template <int RMAX, typename S>
 __global__ void __launch_bounds__(kThreads, 2)
-tikhonov_iter_kernel(float *__restrict__ u, float *__restrict__ d, const float *__restrict__ b,
+tikhonov_iter_kernel(S *__restrict__ u, S *__restrict__ d, const float *__restrict__ b,
                      const uint32_t *__restrict__ words, int wstride, int HW, int R, int N,
                      float rho, float lam, float gam, float *__restrict__ v_out,
                      float *__restrict__ vprev, double *__restrict__ partials)
@@ -159,7 +160,7 @@ tikhonov_iter_kernel(float *__restrict__ u, float *__restrict__ d, const float *
     const float den = 2.f * lam + rho + 2.f * gam;
     double sdv = 0.0, sv = 0.0;
     if (p < HW) {
-        float prev = gam > 0.f ? u[(Z - 1) * HW + p] : 0.f;  // u_{Z-1}, not yet updated
+        float prev = gam > 0.f ? ld<S>(u + (Z - 1) * HW + p) : 0.f;  // u_{Z-1}, not yet updated
         float first_new = 0.f;
         for (int j = 0; j < N; ++j) {
             const uint32_t word = words[j * wstride + p];
@@ -169,8 +170,8 @@ tikhonov_iter_kernel(float *__restrict__ u, float *__restrict__ d, const float *
 #pragma unroll
             for (int r = 0; r < RMAX; ++r) {
                 if (r < R) {
-                    ur[r] = u[base + r * HW];
-                    dr[r] = d[base + r * HW];
+                    ur[r] = ld<S>(u + base + r * HW);
+                    dr[r] = ld<S>(d + base + r * HW);
                     if (bit(word, r)) s += ur[r] - dr[r];
                 }
             }
@@ -188,15 +189,15 @@ tikhonov_iter_kernel(float *__restrict__ u, float *__restrict__ d, const float *
                         float next;
                         if (n == Z - 1) next = first_new;
                         else if (r + 1 < R) next = ur[r + 1 < RMAX ? r + 1 : r];
-                        else next = u[o + HW];  // first plane of the next shot, still old
-                        un = (rho * w + gam * (prev + next)) / den;
+                        else next = ld<S>(u + o + HW);  // next shot's first plane, still old
+                        un = rnd<S>((rho * w + gam * (prev + next)) / den);
                         prev = un;
                         if (n == 0) first_new = un;
                     } else {
                         un = rho * w / den;
                     }
-                    u[o] = un;
-                    d[o] = w - un;
+                    st<S>(u + o, un);
+                    st<S>(d + o, w - un);
                     if (v_out) v_out[o] = v;
                     if (vprev) {
                         const double vp = vprev[o];
@@ -322,18 +323,17 @@ cslsm_status launch_adjoint(const Geom &g, Masks m, const float *b, float *v, cu
     return CSLSM_OK;
 }
 
-cslsm_status launch_xupdate_w(const Geom &g, Masks m, const float *u, const float *d,
-                              const float *b, float rho, float *w, float *v_out, float *vprev,
-                              double *partials, int nblocks_red, cudaStream_t s)
+template <typename S>
+cslsm_status xupdate_typed(const Geom &g, Masks m, const void *u_, const void *d_, const float *b,
+                           float rho, void *w_, float *v_out, float *vprev, double *partials,
+                           cudaStream_t s)
 {
+    const S *u = (const S *)u_, *d = (const S *)d_;
+    S *w = (S *)w_;
     const dim3 grid = pixel_grid(g.HW(), g.N);
-    if (partials && (int)(grid.x * grid.y) > nblocks_red) {
-        set_error("reduction buffer too small");
-        return CSLSM_ERR_INVALID_ARG;
-    }
-#define XU(RM)                                                                                \
-    xupdate_w_kernel<RM><<<grid, kThreads, 0, s>>>(u, d, b, m.words, m.wstride, g.HW(), g.R, \
-                                                   rho, w, v_out, vprev, partials)
+#define XU(RM)                                                                          \
+    xupdate_w_kernel<RM, S><<<grid, kThreads, 0, s>>>(u, d, b, m.words, m.wstride, g.HW(), \
+                                                      g.R, rho, w, v_out, vprev, partials)
     LaunchScope ls(K_XUPDATE, s);
     if (g.R <= 4) XU(4);
     else if (g.R <= 8) XU(8);
@@ -344,18 +344,17 @@ cslsm_status launch_xupdate_w(const Geom &g, Masks m, const float *u, const floa
     return CSLSM_OK;
 }
 
-cslsm_status launch_tikhonov_iter(const Geom &g, Masks m, float *u, float *d, const float *b,
-                                  float rho, float lam, float gam, float *v_out, float *vprev,
-                                  double *partials, int nblocks_red, cudaStream_t s)
+template <typename S>
+cslsm_status tikhonov_typed(const Geom &g, Masks m, void *u_, void *d_, const float *b,
+                            float rho, float lam, float gam, float *v_out, float *vprev,
+                            double *partials, cudaStream_t s)
 {
+    S *u = (S *)u_, *d = (S *)d_;
     const dim3 grid = pixel_grid(g.HW(), 1);
-    if (partials && (int)grid.x > nblocks_red) {
-        set_error("reduction buffer too small");
-        return CSLSM_ERR_INVALID_ARG;
-    }
-#define TK(RM)                                                                                 \
-    tikhonov_iter_kernel<RM><<<grid, kThreads, 0, s>>>(u, d, b, m.words, m.wstride, g.HW(), g.R, \
-                                                       g.N, rho, lam, gam, v_out, vprev, partials)
+#define TK(RM)                                                                            \
+    tikhonov_iter_kernel<RM, S><<<grid, kThreads, 0, s>>>(u, d, b, m.words, m.wstride,   \
+                                                          g.HW(), g.R, g.N, rho, lam, gam, \
+                                                          v_out, vprev, partials)
     LaunchScope ls(K_TIK_ITER, s);
     if (g.R <= 4) TK(4);
     else if (g.R <= 8) TK(8);
@@ -364,6 +363,45 @@ cslsm_status launch_tikhonov_iter(const Geom &g, Masks m, float *u, float *d, co
 #undef TK
     CSLSM_LAUNCHED();
     return CSLSM_OK;
+}
+
+cslsm_status launch_xupdate_w(const Geom &g, Masks m, int storage, const void *u, const void *d,
+                              const float *b, float rho, void *w, float *v_out, float *vprev,
+                              double *partials, int nblocks_red, cudaStream_t s)
+{
+    const dim3 grid = pixel_grid(g.HW(), g.N);
+    if (partials && (int)(grid.x * grid.y) > nblocks_red) {
+        set_error("reduction buffer too small");
+        return CSLSM_ERR_INVALID_ARG;
+    }
+    switch (storage) {
+    case CSLSM_STORE_BF16:
+        return xupdate_typed<__nv_bfloat16>(g, m, u, d, b, rho, w, v_out, vprev, partials, s);
+    case CSLSM_STORE_FP16:
+        return xupdate_typed<__half>(g, m, u, d, b, rho, w, v_out, vprev, partials, s);
+    default:
+        return xupdate_typed<float>(g, m, u, d, b, rho, w, v_out, vprev, partials, s);
+    }
+}
+
+cslsm_status launch_tikhonov_iter(const Geom &g, Masks m, int storage, void *u, void *d,
+                                  const float *b, float rho, float lam, float gam, float *v_out,
+                                  float *vprev, double *partials, int nblocks_red, cudaStream_t s)
+{
+    const dim3 grid = pixel_grid(g.HW(), 1);
+    if (partials && (int)grid.x > nblocks_red) {
+        set_error("reduction buffer too small");
+        return CSLSM_ERR_INVALID_ARG;
+    }
+    switch (storage) {
+    case CSLSM_STORE_BF16:
+        return tikhonov_typed<__nv_bfloat16>(g, m, u, d, b, rho, lam, gam, v_out, vprev,
+                                             partials, s);
+    case CSLSM_STORE_FP16:
+        return tikhonov_typed<__half>(g, m, u, d, b, rho, lam, gam, v_out, vprev, partials, s);
+    default:
+        return tikhonov_typed<float>(g, m, u, d, b, rho, lam, gam, v_out, vprev, partials, s);
+    }
 }
 
 cslsm_status launch_tikhonov_prox(const float *in, float *out, long long n, float rho, float lam,

@@ -17,13 +17,15 @@
 // two neighbouring u slices when gamma > 0) and one write of u and d.
 //
 // Inside a step every warp walks a band of rows top to bottom, one row per
-// iteration, with lane = column: q of the next row is computed once and
-// carried in a register, the right neighbour's q comes from a warp shuffle,
-// so a pixel-step costs 4 shared loads and 2 stores.  Warps own 31 of their
-// 32 columns (column chunks overlap by one, the 32nd lane only supplies q to
-// its left neighbour).  p is double-buffered in shared memory, so one
-// __syncthreads per step suffices, and the row bands are re-balanced every
-// step as the valid region shrinks by one pixel per side.  The Neumann
+// iteration; each lane owns two adjacent columns (float2 shared accesses).
+// q of the next row is computed once and carried in registers, the right
+// neighbour's q and the left neighbour's p come from warp shuffles, so a
+// pixel-step costs 1.5 shared loads and 1 store.  A warp spans 64 columns
+// and owns 62 of them (column chunks overlap by two so that every chunk
+// starts on an even column; the last lane only supplies q and p to its
+// neighbours).  p is double-buffered in shared memory,
+// so one __syncthreads per step suffices, and the row bands are re-balanced
+// every step as the valid region shrinks by one pixel per side.  The Neumann
 // boundary and the outside of the image are handled without branches:
 // gradient components are multiplied by a 0/1 row / column mask, which keeps
 // p = 0 wherever the discrete gradient vanishes.
@@ -34,29 +36,32 @@
 
 #include <algorithm>
 #include <cmath>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "internal.cuh"
+#include "storage.cuh"
 
 namespace cslsm {
 namespace {
 
 constexpr int kMaxSteps = 24;
-constexpr int kBands = 8;  // row bands per CTA (warps per column chunk)
 
 struct TvLaunch {
-    const float *w;
-    float *u;
-    float *d;
+    const void *w;  // element type S of the kernel instantiation
+    void *u;
+    void *d;
     const float *pin;  // [2][nslices][H][W] dual field entering this launch, or null (p = 0)
     float *pout;       // [2][nslices][H][W] dual field leaving it (write_final == 0)
     int H, W, Z, n0, nslices;
     int T;             // steps in this launch
-    int TH, TW, RH;    // tile rows / columns, region rows (region columns: 31 C + 1)
+    int TH, TW, RH;    // tile rows / columns, region rows (region columns: 62 C + 2)
     float rho, gamma, inv_rho2g;
     float theta, inv_theta, tau;
     int write_final;
+    int storage;
 };
 
 __device__ __forceinline__ float sqrt_approx(float x)
@@ -73,16 +78,43 @@ __device__ __forceinline__ float rcp_approx(float x)
     return y;
 }
 
-template <int C>
-__global__ void __launch_bounds__(C * kBands * 32) tv_tile_kernel(const TvLaunch a)
+// Region of RH rows x RW = 62 C + 2 columns, rows stored with pitch PW = 64 C
+// floats (the columns beyond RW stay zero).  Every array starts 2 floats into its allocation so that column -1
+// (read as the left neighbour of column 0, never updated) is addressable.
+template <int C, int B>
+struct Region {
+    static constexpr int RW = 62 * C + 2;
+    static constexpr int PW = 64 * C;
+    static constexpr int NT = C * B * 32;
+    __host__ __device__ static size_t array_floats(int RH) { return (size_t)PW * RH + 4; }
+};
+
+// One Chambolle update of the two columns a lane owns at row i.
+__device__ __forceinline__ float2 chambolle_pair(float2 qc, float2 qn, float qr, float2 pc,
+                                                 float mr, float mc0, float mc1, float tau,
+                                                 float2 &p2c)
 {
-    constexpr int RW = 31 * C + 1;
-    constexpr int NT = C * kBands * 32;
+    const float gx0 = (qn.x - qc.x) * mr, gy0 = (qc.y - qc.x) * mc0;
+    const float gx1 = (qn.y - qc.y) * mr, gy1 = (qr - qc.y) * mc1;
+    const float i0 = rcp_approx(fmaf(tau, sqrt_approx(fmaf(gx0, gx0, gy0 * gy0)), 1.f));
+    const float i1 = rcp_approx(fmaf(tau, sqrt_approx(fmaf(gx1, gx1, gy1 * gy1)), 1.f));
+    p2c = make_float2(fmaf(tau, gy0, p2c.x) * i0, fmaf(tau, gy1, p2c.y) * i1);
+    return make_float2(fmaf(tau, gx0, pc.x) * i0, fmaf(tau, gx1, pc.y) * i1);
+}
+
+// C column chunks of 62 owned columns, B row bands: C * B warps.
+template <int C, int B, typename S>
+__global__ void __launch_bounds__(C * B * 32) tv_tile_kernel(const TvLaunch a)
+{
+    constexpr int kBands = B;
+    using Rg = Region<C, B>;
+    constexpr int RW = Rg::RW, PW = Rg::PW, NT = Rg::NT;
     extern __shared__ float smem[];
-    const int T = a.T, RH = a.RH, RA = RW * RH;
-    float *sg = smem;
-    float *A1 = sg + RA, *A2 = A1 + RA;  // p^t   (components along rows / columns)
-    float *B1 = A2 + RA, *B2 = B1 + RA;  // p^t+1
+    const int T = a.T, RH = a.RH;
+    const size_t AF = Rg::array_floats(RH);
+    float *sg = smem + 2;
+    float *A1 = sg + AF, *A2 = A1 + AF;  // p^t   (components along rows / columns)
+    float *B1 = A2 + AF, *B2 = B1 + AF;  // p^t+1
     const int sl = blockIdx.z;
     const int n = a.n0 + sl;
     const int H = a.H, W = a.W;
@@ -90,20 +122,23 @@ __global__ void __launch_bounds__(C * kBands * 32) tv_tile_kernel(const TvLaunch
     const int gi0 = blockIdx.y * a.TH - (T + 1);
     const int gj0 = blockIdx.x * a.TW - (T + 1);
 
-    const float *wn = a.w + (size_t)n * HW;
-    const float *um = a.u + (size_t)((n + a.Z - 1) % a.Z) * HW;
-    const float *up = a.u + (size_t)((n + 1) % a.Z) * HW;
+    const S *wn = (const S *)a.w + (size_t)n * HW;
+    const S *um = (const S *)a.u + (size_t)((n + a.Z - 1) % a.Z) * HW;
+    const S *up = (const S *)a.u + (size_t)((n + 1) % a.Z) * HW;
     const float *p1in = a.pin ? a.pin + (size_t)sl * HW : nullptr;
     const float *p2in = a.pin ? a.pin + (size_t)(a.nslices + sl) * HW : nullptr;
 
-    for (int idx = threadIdx.x; idx < RA; idx += NT) {
-        const int li = idx / RW, lj = idx - li * RW;
+    if (threadIdx.x < 2)  // column -1 of row 0 .. and the pads: zero
+        for (int k = 0; k < 5; ++k) smem[k * AF + threadIdx.x] = 0.f;
+    for (int idx = threadIdx.x; idx < RH * PW; idx += NT) {
+        const int li = idx / PW, lj = idx - li * PW;
         const int gi = gi0 + li, gj = gj0 + lj;
         float g = 0.f, p1 = 0.f, p2 = 0.f;
-        if (gi >= 0 && gi < H && gj >= 0 && gj < W) {
+        if (lj < RW && gi >= 0 && gi < H && gj >= 0 && gj < W) {
             const size_t o = (size_t)gi * W + gj;
-            const float wv = wn[o];
-            g = a.gamma > 0.f ? (a.rho * wv + a.gamma * (um[o] + up[o])) * a.inv_rho2g : wv;
+            const float wv = ld<S>(wn + o);
+            g = a.gamma > 0.f ? (a.rho * wv + a.gamma * (ld<S>(um + o) + ld<S>(up + o))) * a.inv_rho2g
+                              : wv;
             if (p1in) {
                 p1 = p1in[o];
                 p2 = p2in[o];
@@ -112,40 +147,61 @@ __global__ void __launch_bounds__(C * kBands * 32) tv_tile_kernel(const TvLaunch
         sg[idx] = g;
         A1[idx] = p1;
         A2[idx] = p2;
+        B1[idx] = 0.f;
+        B2[idx] = 0.f;
     }
     __syncthreads();
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int chunk = warp % C, band = warp / C;
-    const int j = chunk * 31 + lane;   // local column, 0 .. RW-1
-    const int jl = j > 0 ? j - 1 : 0;  // left neighbour (clamped for column 0, never updated)
-    const int gj = gj0 + j;
-    const float mc = (gj >= 0 && gj < W - 1) ? 1.f : 0.f;
+    const int j0 = chunk * 62 + 2 * lane;  // local columns j0, j0 + 1 (even: float2)
+    const int gj = gj0 + j0;
+    const float mc0 = (gj >= 0 && gj < W - 1) ? 1.f : 0.f;
+    const float mc1 = (gj + 1 >= 0 && gj + 1 < W - 1) ? 1.f : 0.f;
     const float inv_theta = a.inv_theta, tau = a.tau;
+    const unsigned Hm1 = (unsigned)(H - 1);
 
     for (int s = 0; s < T; ++s) {
         const int lo = s + 1, len = RH - 2 * s - 3;  // p^{s+1} rows [s+1, RH-s-2)
         const int r0 = lo + (band * len) / kBands;
         const int r1 = lo + ((band + 1) * len) / kBands;
-        const bool upd = lane < 31 && j >= lo && j < RW - s - 2;
         if (r0 < r1) {
-            float p1c = A1[r0 * RW + j], p2c = A2[r0 * RW + j];
-            float qc = fmaf(-sg[r0 * RW + j], inv_theta,
-                            (p1c - A1[(r0 - 1) * RW + j]) + (p2c - A2[r0 * RW + jl]));
-            int gi = gi0 + r0;
+            const float *a1 = A1 + r0 * PW + j0, *a2 = A2 + r0 * PW + j0, *gg = sg + r0 * PW + j0;
+            float *b1 = B1 + r0 * PW + j0, *b2 = B2 + r0 * PW + j0;
+            float2 p1c = *reinterpret_cast<const float2 *>(a1);
+            float2 p2c = *reinterpret_cast<const float2 *>(a2);
+            float2 qc;
+            {
+                const float2 p1u = *reinterpret_cast<const float2 *>(a1 - PW);
+                const float2 gc = *reinterpret_cast<const float2 *>(gg);
+                float p2l = __shfl_up_sync(0xffffffffu, p2c.y, 1);
+                if (lane == 0) p2l = a2[-1];
+                qc.x = fmaf(-gc.x, inv_theta, (p1c.x - p1u.x) + (p2c.x - p2l));
+                qc.y = fmaf(-gc.y, inv_theta, (p1c.y - p1u.y) + (p2c.y - p2c.x));
+            }
+            unsigned gi = (unsigned)(gi0 + r0);
             for (int i = r0; i < r1; ++i, ++gi) {
-                const int o = (i + 1) * RW;
-                const float p1n = A1[o + j], p2n = A2[o + j];
-                const float qn = fmaf(-sg[o + j], inv_theta, (p1n - p1c) + (p2n - A2[o + jl]));
-                const float qr = __shfl_down_sync(0xffffffffu, qc, 1);
-                const float mr = (gi >= 0 && gi < H - 1) ? 1.f : 0.f;
-                const float gx = (qn - qc) * mr;
-                const float gy = (qr - qc) * mc;
-                const float inv = rcp_approx(fmaf(tau, sqrt_approx(fmaf(gx, gx, gy * gy)), 1.f));
-                if (upd) {
-                    B1[i * RW + j] = fmaf(tau, gx, p1c) * inv;
-                    B2[i * RW + j] = fmaf(tau, gy, p2c) * inv;
+                a1 += PW;
+                a2 += PW;
+                gg += PW;
+                const float2 p1n = *reinterpret_cast<const float2 *>(a1);
+                const float2 p2n = *reinterpret_cast<const float2 *>(a2);
+                const float2 gn = *reinterpret_cast<const float2 *>(gg);
+                float p2l = __shfl_up_sync(0xffffffffu, p2n.y, 1);
+                if (lane == 0) p2l = a2[-1];
+                float2 qn;
+                qn.x = fmaf(-gn.x, inv_theta, (p1n.x - p1c.x) + (p2n.x - p2l));
+                qn.y = fmaf(-gn.y, inv_theta, (p1n.y - p1c.y) + (p2n.y - p2n.x));
+                const float qr = __shfl_down_sync(0xffffffffu, qc.x, 1);
+                const float mr = gi < Hm1 ? 1.f : 0.f;
+                float2 p2new = p2c;
+                const float2 p1new = chambolle_pair(qc, qn, qr, p1c, mr, mc0, mc1, tau, p2new);
+                if (lane < 31) {  // lane 31's columns belong to the next chunk
+                    *reinterpret_cast<float2 *>(b1) = p1new;
+                    *reinterpret_cast<float2 *>(b2) = p2new;
                 }
+                b1 += PW;
+                b2 += PW;
                 qc = qn;
                 p1c = p1n;
                 p2c = p2n;
@@ -165,13 +221,13 @@ __global__ void __launch_bounds__(C * kBands * 32) tv_tile_kernel(const TvLaunch
         const int ti = idx / TW, tj = idx - ti * TW;
         const int gi = gi0 + T + 1 + ti, gjj = gj0 + T + 1 + tj;
         if (gi >= H || gjj >= W) continue;
-        const int l = (T + 1 + ti) * RW + (T + 1 + tj);
+        const int l = (T + 1 + ti) * PW + (T + 1 + tj);
         const size_t o = (size_t)gi * W + gjj;
         if (a.write_final) {
-            const float divp = (A1[l] - A1[l - RW]) + (A2[l] - A2[l - 1]);
+            const float divp = (A1[l] - A1[l - PW]) + (A2[l] - A2[l - 1]);
             const float uv = sg[l] - a.theta * divp;
-            a.u[(size_t)n * HW + o] = uv;
-            if (a.d) a.d[(size_t)n * HW + o] = wn[o] - uv;
+            st<S>((S *)a.u + (size_t)n * HW + o, uv);
+            if (a.d) st<S>((S *)a.d + (size_t)n * HW + o, ld<S>(wn + o) - rnd<S>(uv));
         } else {
             a.pout[(size_t)sl * HW + o] = A1[l];
             a.pout[(size_t)(a.nslices + sl) * HW + o] = A2[l];
@@ -179,96 +235,207 @@ __global__ void __launch_bounds__(C * kBands * 32) tv_tile_kernel(const TvLaunch
     }
 }
 
-inline size_t smem_bytes(int C, int RH) { return 5ull * (31 * C + 1) * RH * sizeof(float); }
+inline size_t smem_bytes(int C, int RH)
+{
+    return 5ull * ((size_t)64 * C * RH + 4) * sizeof(float);
+}
 
 constexpr size_t kSmemLimit = 227 * 1024;  // per CTA
 constexpr size_t kSmemPerSm = 228 * 1024;
 
+// Kernel variants: (column chunks, row bands).
+struct Variant {
+    int C, B;
+};
+constexpr Variant kVariants[] = {{1, 12}, {1, 24}, {2, 12}, {2, 16}};
+constexpr int kNumVariants = 4;
+
 struct Shape {
-    int C, TH, TW, RH;
+    int v, TH, TW, RH;  // variant index, tile rows / columns, region rows
 };
 
-// Per-device state: SM count and the kernels' shared-memory opt-in.
+std::mutex g_mu;
 struct DeviceInfo {
     int sms = 0;
     bool ready = false;
 };
-std::mutex g_mu;
 std::vector<DeviceInfo> g_dev;
+int g_mode = 0;  // 0: cost model, 1: timed autotuning, 2 + k: force variant k
+struct Key {
+    int dev, H, W, T, ns;
+    bool operator<(const Key &o) const
+    {
+        return std::tie(dev, H, W, T, ns) < std::tie(o.dev, o.H, o.W, o.T, o.ns);
+    }
+};
+std::map<Key, Shape> g_tuned;
 
-cslsm_status device_info(int &sms)
+template <int C, int B>
+cslsm_status set_attr()
 {
-    int dev = 0;
+    const int lim = (int)kSmemLimit;
+    CSLSM_CUDA(cudaFuncSetAttribute(tv_tile_kernel<C, B, float>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    CSLSM_CUDA(cudaFuncSetAttribute(tv_tile_kernel<C, B, __nv_bfloat16>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    CSLSM_CUDA(cudaFuncSetAttribute(tv_tile_kernel<C, B, __half>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    return CSLSM_OK;
+}
+
+cslsm_status device_info(int &dev, int &sms)
+{
     CSLSM_CUDA(cudaGetDevice(&dev));
     std::lock_guard<std::mutex> lk(g_mu);
     if ((int)g_dev.size() <= dev) g_dev.resize(dev + 1);
     DeviceInfo &di = g_dev[dev];
     if (!di.ready) {
         CSLSM_CUDA(cudaDeviceGetAttribute(&di.sms, cudaDevAttrMultiProcessorCount, dev));
-        const int lim = (int)kSmemLimit;
-        CSLSM_CUDA(cudaFuncSetAttribute(tv_tile_kernel<1>,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-        CSLSM_CUDA(cudaFuncSetAttribute(tv_tile_kernel<2>,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-        CSLSM_CUDA(cudaFuncSetAttribute(tv_tile_kernel<3>,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-        CSLSM_CUDA(cudaFuncSetAttribute(tv_tile_kernel<4>,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+        cslsm_status e;
+        if ((e = set_attr<1, 12>()) || (e = set_attr<1, 24>()) || (e = set_attr<2, 12>()) ||
+            (e = set_attr<2, 16>()))
+            return e;
         di.ready = true;
     }
     sms = di.sms;
     return CSLSM_OK;
 }
 
-// Tile shape with the least estimated time: waves of CTAs over the SMs times
-// the pixel-steps one CTA performs on its shrinking region.
-Shape pick_shape(int H, int W, int T, int nslices, int sms)
+// Best tile rows for one variant under the cost model: waves of CTAs times the
+// pixel-steps of one CTA's shrinking region, with a latency penalty when fewer
+// than 32 warps share an SM.  Returns the modelled cost (inf if nothing fits).
+double model_shape(int vi, int H, int W, int T, int nslices, int sms, Shape &out)
 {
-    Shape best{0, 0, 0, 0};
-    double best_cost = 1e300;
-    for (int C = 1; C <= 4; ++C) {
-        const int RW = 31 * C + 1;
-        const int TW = RW - 2 * T - 2;
-        if (TW < 8) continue;
-        const int tiles_w = (W + TW - 1) / TW;
-        const int threads = C * kBands * 32;
-        for (int TH = 8; TH <= 512; TH += 2) {
-            const int RH = TH + 2 * T + 2;
-            const size_t sm = smem_bytes(C, RH);
-            if (sm > kSmemLimit) break;
-            const int per_sm = (int)std::min<size_t>(kSmemPerSm / (sm + 1024), 2048 / threads);
-            if (per_sm < 1) break;
-            const long long ctas = (long long)tiles_w * ((H + TH - 1) / TH) * nslices;
-            const double waves = std::ceil((double)ctas / ((double)sms * per_sm));
-            double work = 2.0 * RW * RH;  // pixel-steps of one CTA plus its load
-            for (int s = 0; s < T; ++s) work += (double)(RW - 2 * s - 3) * (RH - 2 * s - 3);
-            const double cost = waves * work * per_sm;
-            if (cost < best_cost) {
-                best_cost = cost;
-                best = Shape{C, TH, TW, RH};
-            }
-            if (TH >= H) break;
+    const int C = kVariants[vi].C, B = kVariants[vi].B;
+    const int RW = 62 * C + 2, TW = RW - 2 * T - 2;
+    double best = 1e300;
+    if (TW < 4) return best;
+    const int tiles_w = (W + TW - 1) / TW, threads = C * B * 32;
+    for (int TH = 4; TH <= 1024; TH += 2) {
+        const int RH = TH + 2 * T + 2;
+        const size_t sm = smem_bytes(C, RH);
+        if (sm > kSmemLimit) break;
+        const int per_sm = (int)std::min<size_t>(kSmemPerSm / (sm + 1024), 2048 / threads);
+        if (per_sm < 1) break;
+        const long long ctas = (long long)tiles_w * ((H + TH - 1) / TH) * nslices;
+        const int resident = (int)std::min<long long>(per_sm, (ctas + sms - 1) / sms);
+        const double waves = std::ceil((double)ctas / ((double)sms * per_sm));
+        double work = 2.0 * RW * RH;  // pixel-steps of one CTA plus its load
+        for (int s = 0; s < T; ++s) work += (double)(RW - 2 * s - 3) * (RH - 2 * s - 3);
+        const double warps = (double)resident * C * B;
+        const double cost = waves * work * per_sm * std::max(1.0, 32.0 / warps);
+        if (cost < best) {
+            best = cost;
+            out = Shape{vi, TH, TW, RH};
         }
+        if (TH >= H) break;
     }
     return best;
 }
 
+template <typename S>
+void launch_variant(int v, dim3 grid, int nt, size_t sm, cudaStream_t st, const TvLaunch &b)
+{
+    switch (v) {
+    case 0: tv_tile_kernel<1, 12, S><<<grid, nt, sm, st>>>(b); break;
+    case 1: tv_tile_kernel<1, 24, S><<<grid, nt, sm, st>>>(b); break;
+    case 2: tv_tile_kernel<2, 12, S><<<grid, nt, sm, st>>>(b); break;
+    default: tv_tile_kernel<2, 16, S><<<grid, nt, sm, st>>>(b); break;
+    }
+}
+
 cslsm_status launch_tile(const TvLaunch &a, const Shape &sh, cudaStream_t st)
 {
-    if (sh.C < 1) {
+    if (sh.RH <= 0) {
         set_error("no TV tile shape fits shared memory for %d steps", a.T);
         return CSLSM_ERR_UNSUPPORTED;
     }
+    TvLaunch b = a;
+    b.TH = sh.TH;
+    b.TW = sh.TW;
+    b.RH = sh.RH;
+    const Variant v = kVariants[sh.v];
     const dim3 grid((a.W + sh.TW - 1) / sh.TW, (a.H + sh.TH - 1) / sh.TH, a.nslices);
-    const size_t sm = smem_bytes(sh.C, sh.RH);
+    const size_t sm = smem_bytes(v.C, sh.RH);
+    const int nt = v.C * v.B * 32;
     LaunchScope ls(K_TV_TILE, st);
-    switch (sh.C) {
-    case 1: tv_tile_kernel<1><<<grid, 1 * kBands * 32, sm, st>>>(a); break;
-    case 2: tv_tile_kernel<2><<<grid, 2 * kBands * 32, sm, st>>>(a); break;
-    case 3: tv_tile_kernel<3><<<grid, 3 * kBands * 32, sm, st>>>(a); break;
-    default: tv_tile_kernel<4><<<grid, 4 * kBands * 32, sm, st>>>(a); break;
-    }
+    if (a.storage == CSLSM_STORE_BF16) launch_variant<__nv_bfloat16>(sh.v, grid, nt, sm, st, b);
+    else if (a.storage == CSLSM_STORE_FP16) launch_variant<__half>(sh.v, grid, nt, sm, st, b);
+    else launch_variant<float>(sh.v, grid, nt, sm, st, b);
     CSLSM_LAUNCHED();
+    return CSLSM_OK;
+}
+
+// Shape for this launch: forced variant, cached tuning result, cost model, or
+// (mode 1, outside stream capture, first use of the key) timed candidates.
+cslsm_status choose_shape(const TvLaunch &a, int dev, int sms, cudaStream_t st, bool may_time,
+                          Shape &sh)
+{
+    int mode;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        mode = g_mode;
+        if (mode == 1 && !may_time) mode = 0;
+        if (mode == 1) {
+            auto it = g_tuned.find(Key{dev, a.H, a.W, a.T, a.nslices});
+            if (it != g_tuned.end()) {
+                sh = it->second;
+                return CSLSM_OK;
+            }
+        }
+    }
+    Shape cand[kNumVariants];
+    double cost[kNumVariants];
+    int best = -1;
+    for (int v = 0; v < kNumVariants; ++v) {
+        cand[v] = Shape{v, 0, 0, 0};
+        cost[v] = model_shape(v, a.H, a.W, a.T, a.nslices, sms, cand[v]);
+        if (cost[v] < 1e300 && (best < 0 || cost[v] < cost[best])) best = v;
+    }
+    if (mode >= 2) {
+        const int v = (mode - 2) % kNumVariants;
+        if (cost[v] < 1e300) best = v;
+    }
+    if (best < 0) {
+        set_error("no TV tile shape fits shared memory for %d steps", a.T);
+        return CSLSM_ERR_UNSUPPORTED;
+    }
+    sh = cand[best];
+    if (mode != 1) return CSLSM_OK;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CSLSM_CUDA(cudaStreamIsCapturing(st, &cap));
+    if (cap != cudaStreamCaptureStatusNone) return CSLSM_OK;
+    // time every variant (the launch is idempotent: same inputs, same outputs)
+    cudaEvent_t e0, e1;
+    CSLSM_CUDA(cudaEventCreate(&e0));
+    CSLSM_CUDA(cudaEventCreate(&e1));
+    float best_ms = 1e30f;
+    for (int v = 0; v < kNumVariants; ++v) {
+        if (cost[v] >= 1e300) continue;
+        float ms_min = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+            cudaEventRecord(e0, st);
+            cslsm_status e = launch_tile(a, cand[v], st);
+            cudaEventRecord(e1, st);
+            if (e) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return e;
+            }
+            float ms = 0.f;
+            if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) ==
+                                                               cudaSuccess)
+                ms_min = std::min(ms_min, ms);
+        }
+        if (ms_min < best_ms) {
+            best_ms = ms_min;
+            sh = cand[v];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_tuned[Key{dev, a.H, a.W, a.T, a.nslices}] = sh;
     return CSLSM_OK;
 }
 
@@ -276,12 +443,53 @@ cslsm_status launch_tile(const TvLaunch &a, const Shape &sh, cudaStream_t st)
 
 int tv_max_steps_per_launch() { return kMaxSteps; }
 
-cslsm_status tv_prox_slices(const TvSlices &s, float *pbuf, cudaStream_t st)
+cslsm_status tv_query_shape(int H, int W, int T, int nslices, int *out4)
 {
-    int sms = 0;
-    cslsm_status e = device_info(sms);
+    int dev = 0, sms = 0;
+    cslsm_status e = device_info(dev, sms);
     if (e) return e;
     TvLaunch a{};
+    a.H = H;
+    a.W = W;
+    a.T = T;
+    a.nslices = nslices;
+    Shape sh{};
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (g_mode == 1) {
+            auto it = g_tuned.find(Key{dev, H, W, T, nslices});
+            if (it != g_tuned.end()) {
+                sh = it->second;
+                out4[0] = sh.v;
+                out4[1] = sh.TH;
+                out4[2] = sh.TW;
+                out4[3] = sh.RH;
+                return CSLSM_OK;
+            }
+        }
+    }
+    if ((e = choose_shape(a, dev, sms, nullptr, false, sh))) return e;
+    out4[0] = sh.v;
+    out4[1] = sh.TH;
+    out4[2] = sh.TW;
+    out4[3] = sh.RH;
+    return CSLSM_OK;
+}
+
+void tv_set_mode(int mode)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_mode = mode;
+    if (mode != 1) g_tuned.clear();
+}
+
+cslsm_status tv_prox_slices(const TvSlices &s, float *pbuf, cudaStream_t st)
+{
+    int dev = 0, sms = 0;
+    cslsm_status e = device_info(dev, sms);
+    if (e) return e;
+    TvLaunch a{};
+    a.storage = s.storage;
     a.w = s.w;
     a.u = s.u;
     a.d = s.d;
@@ -298,12 +506,10 @@ cslsm_status tv_prox_slices(const TvSlices &s, float *pbuf, cudaStream_t st)
     a.tau = s.tau;
     const int T = s.theta > 0.f ? s.T : 0;  // zero weight: the prox is the identity
     if (T <= kMaxSteps) {
-        const Shape sh = pick_shape(s.H, s.W, T, s.nslices, sms);
         a.T = T;
-        a.TH = sh.TH;
-        a.TW = sh.TW;
-        a.RH = sh.RH;
         a.write_final = 1;
+        Shape sh{};
+        if ((e = choose_shape(a, dev, sms, st, true, sh))) return e;
         return launch_tile(a, sh, st);
     }
     if (!pbuf) {
@@ -316,14 +522,12 @@ cslsm_status tv_prox_slices(const TvSlices &s, float *pbuf, cudaStream_t st)
     int done = 0;
     for (int c = 0; c < nch; ++c) {
         const int steps = (T - done) / (nch - c);
-        const Shape sh = pick_shape(s.H, s.W, steps, s.nslices, sms);
         a.T = steps;
-        a.TH = sh.TH;
-        a.TW = sh.TW;
-        a.RH = sh.RH;
         a.pin = pin;
         a.write_final = (c == nch - 1);
         a.pout = a.write_final ? nullptr : pbuf + (c % 2) * half;
+        Shape sh{};
+        if ((e = choose_shape(a, dev, sms, st, false, sh))) return e;
         e = launch_tile(a, sh, st);
         if (e) return e;
         pin = a.pout;

@@ -87,6 +87,25 @@ def test_denoise_tv(cs, shape, T, lam):
     assert rel_l2(out, ref) <= REL_ITER
 
 
+@pytest.mark.parametrize("mode", [2, 3, 4, 5, 1])
+@pytest.mark.parametrize("shape,T", [((3, 70, 45), 20), ((1, 131, 97), 7), ((2, 256, 200), 24)])
+def test_tv_kernel_variants(cs, mode, shape, T):
+    """Every TV kernel variant (forced) and the timed autotuner give the oracle's prox."""
+    rng = np.random.default_rng(T + shape[1])
+    x = rng.random(shape).astype(np.float32)
+    prm = cs.Params(rho=1.0, lam=0.1, tv_inner=T, denoiser="tv")
+    try:
+        cs.set_autotune(mode)
+        out = to_np(cs.denoise(to_dev(x), prm))
+        out2 = to_np(cs.denoise(to_dev(x), prm))  # the tuned (cached) choice
+    finally:
+        cs.set_autotune(0)
+    ref = oracle.tv_prox(x, 0.1, T)
+    assert rel_l2(out, ref) <= REL_ITER
+    np.testing.assert_array_equal(out, out2) if mode >= 2 else None
+    assert rel_l2(out2, ref) <= REL_ITER
+
+
 def test_denoise_tv_zero_weight_is_identity(cs):
     x = np.random.default_rng(0).random((2, 40, 50)).astype(np.float32)
     out = to_np(cs.denoise(to_dev(x), cs.Params(lam=0.0, denoiser="tv")))
