@@ -25,7 +25,9 @@
 //    A CTA owns an 8x8 block of references: it stages g (and the basic
 //    estimate) of the block's footprint in shared memory and aggregates the
 //    block's estimates there with shared atomics before one global atomic
-//    flush per footprint pixel.
+//    flush per footprint pixel.  Numerators and denominators accumulate in
+//    FP64, so the order of the atomics changes sums only at the 1e-16 level and
+//    repeated calls give the same FP32 result.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -290,7 +292,7 @@ struct FilterArgs {
     const float *guide;   // [ns][H][W] basic estimate (Wiener) or null
     const int *lists;     // [ns][nref][16]
     const int *counts;    // [ns][nref]
-    float *num, *den;     // [ns][H][W] accumulators
+    double *num, *den;    // [ns][H][W] accumulators
     int H, W, ns;
     float sigma;
 };
@@ -298,7 +300,7 @@ struct FilterArgs {
 template <bool kWiener>
 __global__ void __launch_bounds__(kFilterWarps * 32) bm3d_filter_kernel(const FilterArgs a)
 {
-    __shared__ float s_num[kFoot * kFootPitch], s_den[kFoot * kFootPitch];
+    __shared__ double s_num[kFoot * kFootPitch], s_den[kFoot * kFootPitch];
     __shared__ float s_n[kFoot * kFootPitch];
     __shared__ float s_b[kWiener ? kFoot * kFootPitch : 1];
     const int H = a.H, W = a.W;
@@ -316,8 +318,8 @@ __global__ void __launch_bounds__(kFilterWarps * 32) bm3d_filter_kernel(const Fi
         const int y = idx / fw, x = idx - y * fw;
         const int l = y * kFootPitch + x;
         const size_t o = (size_t)(f0 + y) * W + g0 + x;
-        s_num[l] = 0.f;
-        s_den[l] = 0.f;
+        s_num[l] = 0.0;
+        s_den[l] = 0.0;
         s_n[l] = noisy[o];
         if (kWiener) s_b[l] = guide[o];
     }
@@ -386,18 +388,18 @@ __global__ void __launch_bounds__(kFilterWarps * 32) bm3d_filter_kernel(const Fi
                 for (int c = 0; c < kPS; ++c) {
                     const int l = (py + 4 * h + rw) * kFootPitch + px + c;
                     const float kw = weight * c_kaiser[(4 * h + rw) * kPS + c];
-                    atomicAdd(&s_num[l], kw * x[rw][c]);
-                    atomicAdd(&s_den[l], kw);
+                    atomicAdd(&s_num[l], (double)(kw * x[rw][c]));
+                    atomicAdd(&s_den[l], (double)kw);
                 }
         }
     }
     __syncthreads();
-    float *num = a.num + sl * HW, *den = a.den + sl * HW;
+    double *num = a.num + sl * HW, *den = a.den + sl * HW;
     for (int idx = threadIdx.x; idx < fh * fw; idx += blockDim.x) {
         const int y = idx / fw, x = idx - y * fw;
         const int l = y * kFootPitch + x;
-        const float d = s_den[l];
-        if (d != 0.f) {
+        const double d = s_den[l];
+        if (d != 0.0) {
             const size_t o = (size_t)(f0 + y) * W + g0 + x;
             atomicAdd(&num[o], s_num[l]);
             atomicAdd(&den[o], d);
@@ -409,7 +411,7 @@ __global__ void __launch_bounds__(kFilterWarps * 32) bm3d_filter_kernel(const Fi
 // accumulators; optionally dual = w - out (the ADMM dual update of the
 // slices) and the 8-bit codes of out for the next stage's matching.
 template <typename S>
-__global__ void bm3d_finish_kernel(float *__restrict__ num, float *__restrict__ den,
+__global__ void bm3d_finish_kernel(double *__restrict__ num, double *__restrict__ den,
                                    S *__restrict__ out, const S *__restrict__ w,
                                    S *__restrict__ dual, uint8_t *__restrict__ codes,
                                    long long N)
@@ -418,11 +420,11 @@ __global__ void bm3d_finish_kernel(float *__restrict__ num, float *__restrict__ 
          i += (long long)gridDim.x * blockDim.x) {
         float v;
         if (den) {
-            v = num[i] / den[i];
-            num[i] = 0.f;
-            den[i] = 0.f;
+            v = (float)(num[i] / den[i]);
+            num[i] = 0.0;
+            den[i] = 0.0;
         } else {
-            v = num[i];
+            v = (float)num[i];
         }
         st<S>(out + i, v);
         if (dual) st<S>(dual + i, ld<S>(w + i) - rnd<S>(v));
@@ -430,6 +432,18 @@ __global__ void bm3d_finish_kernel(float *__restrict__ num, float *__restrict__ 
             const float r = rintf(__fmul_rn(v, 255.f));
             codes[i] = (uint8_t)(r < 0.f ? 0.f : (r > 255.f ? 255.f : r));
         }
+    }
+}
+
+// out = g where no patch fits (the identity), with the same epilogue.
+template <typename S>
+__global__ void bm3d_copy_kernel(const float *__restrict__ g, S *__restrict__ out,
+                                 const S *__restrict__ w, S *__restrict__ dual, long long N)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+         i += (long long)gridDim.x * blockDim.x) {
+        st<S>(out + i, g[i]);
+        if (dual) st<S>(dual + i, ld<S>(w + i) - rnd<S>(g[i]));
     }
 }
 
@@ -478,7 +492,8 @@ inline unsigned grid_for(long long n, int threads)
 
 // Workspace carve-up for ns slices (256-byte aligned pieces).
 struct Ws {
-    float *g, *basic, *num, *den;
+    float *g, *basic;
+    double *num, *den;
     uint8_t *codes;
     int *lists, *counts;
 };
@@ -494,10 +509,10 @@ Ws carve(void *base, int ns, int H, int W)
     p += al(ns * HW * sizeof(float));
     w.basic = (float *)p;
     p += al(ns * HW * sizeof(float));
-    w.num = (float *)p;
-    p += al(ns * HW * sizeof(float));
-    w.den = (float *)p;
-    p += al(ns * HW * sizeof(float));
+    w.num = (double *)p;
+    p += al(ns * HW * sizeof(double));
+    w.den = (double *)p;
+    p += al(ns * HW * sizeof(double));
     w.codes = (uint8_t *)p;
     p += al(ns * HW);
     w.lists = (int *)p;
@@ -544,7 +559,7 @@ cslsm_status filter(int stage, const float *noisy, const float *guide, const Ws 
 }
 
 template <typename S>
-cslsm_status finish(float *num, float *den, S *out, const S *w, S *dual, uint8_t *codes,
+cslsm_status finish(double *num, double *den, S *out, const S *w, S *dual, uint8_t *codes,
                     long long N, cudaStream_t s)
 {
     LaunchScope ls(K_BM3D_FINISH, s);
@@ -570,10 +585,9 @@ cslsm_status slices_typed(const Bm3dSlices &b, void *ws, cudaStream_t s)
         return e;
     if (H < kPS || W < kPS) {  // no patch fits: the denoiser is the identity
         LaunchScope ls(K_BM3D_FINISH, s);
-        bm3d_finish_kernel<float><<<grid_for(N, 256), 256, 0, s>>>(w.g, nullptr, w.basic, nullptr,
-                                                                   nullptr, nullptr, N);
+        bm3d_copy_kernel<S><<<grid_for(N, 256), 256, 0, s>>>(w.g, out, src, dual, N);
         CSLSM_LAUNCHED();
-        return finish<S>(w.basic, nullptr, out, src, dual, nullptr, N, s);
+        return CSLSM_OK;
     }
     if ((e = match(w.codes, ns, H, W, 1, w.lists, w.counts, s))) return e;
     if ((e = filter(1, w.g, nullptr, w, ns, H, W, b.sigma, s))) return e;
@@ -590,7 +604,7 @@ int bm3d_nref(int H, int W) { return n_refs(H) * n_refs(W); }
 size_t bm3d_workspace_bytes(int ns, int H, int W)
 {
     const size_t HW = (size_t)H * W, nref = (size_t)n_refs(H) * n_refs(W);
-    return 4 * al(ns * HW * sizeof(float)) + al(ns * HW) +
+    return 2 * al(ns * HW * sizeof(float)) + 2 * al(ns * HW * sizeof(double)) + al(ns * HW) +
            al(ns * nref * kMaxGroup * sizeof(int)) + al(ns * nref * sizeof(int)) + 256;
 }
 
