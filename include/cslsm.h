@@ -188,6 +188,33 @@ cslsm_status cslsm_bm3d_match(const float *img, int Z, int H, int W, int stage, 
 cslsm_status cslsm_bm3d_stage(int stage, const float *noisy, const float *guide, float *out,
                               int Z, int H, int W, float sigma, void *stream);
 
+/* ---- allocation-free BM3D ------------------------------------------------
+ * The paper has no counterpart to this entry point; it serves callers that
+ * cannot allocate device memory when they denoise (inside a CUDA graph
+ * capture that forbids allocation, under a fixed memory budget owned by the
+ * host application, or in a loop where an allocation's latency or failure is
+ * not acceptable).
+ *
+ * cslsm_denoise_bm3d_noalloc computes exactly what cslsm_denoise does with
+ * the BM3D prior at noise level sigma (in, out: device [Z][H][W], not
+ * overlapping), but its scratch is a fixed array inside the library instead
+ * of cudaMallocAsync memory: it calls no cudaMalloc, cudaFree or other
+ * allocating routine.  The array holds cslsm_bm3d_noalloc_capacity() bytes
+ * (64 MiB) on every GPU that loads the library, until the process exits.  A
+ * call whose scratch (cslsm_bm3d_scratch_bytes(Z, H, W): about 33 bytes per
+ * voxel, e.g. 8.5 MB for one 512 x 512 slice) exceeds it returns
+ * CSLSM_ERR_INVALID_ARG before any GPU work.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  Every call on a device shares the one array and clears
+ * the part it uses at its start, so calls whose GPU work overlaps (on
+ * different streams, or from different host threads) race and give wrong
+ * results; serialise them on one stream. */
+size_t cslsm_bm3d_noalloc_capacity(void);
+size_t cslsm_bm3d_scratch_bytes(int Z, int H, int W);
+cslsm_status cslsm_denoise_bm3d_noalloc(const float *in, float *out, int Z, int H, int W,
+                                        float sigma, void *stream);
+
 /* Volume PSNR of Sec. IV (all voxels as one array): writes
  * 10 log10(n V^2 / ||x - ref||^2), V = max(ref), as a double to out (device).
  * Deterministic two-level reduction; uses a stream-ordered scratch buffer. */

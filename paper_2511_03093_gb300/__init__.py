@@ -110,6 +110,12 @@ def lib() -> ctypes.CDLL:
     L.cslsm_last_error.restype = ctypes.c_char_p
     L.cslsm_abi_version.argtypes = []
     L.cslsm_abi_version.restype = I
+    L.cslsm_bm3d_noalloc_capacity.argtypes = []
+    L.cslsm_bm3d_noalloc_capacity.restype = ctypes.c_size_t
+    L.cslsm_bm3d_scratch_bytes.argtypes = [I, I, I]
+    L.cslsm_bm3d_scratch_bytes.restype = ctypes.c_size_t
+    L.cslsm_denoise_bm3d_noalloc.argtypes = [P, P, I, I, I, F, P]
+    L.cslsm_denoise_bm3d_noalloc.restype = I
     L.cslsm_tv_shape.argtypes = [I, I, I, I, P]
     L.cslsm_tv_shape.restype = I
     L.cslsm_set_autotune.argtypes = [I]
@@ -314,3 +320,20 @@ def tv_shape(H: int, W: int, steps: int, nslices: int) -> dict:
     _check(lib().cslsm_tv_shape(int(H), int(W), int(steps), int(nslices), buf),
            "cslsm_tv_shape")
     return {"variant": buf[0], "tile_rows": buf[1], "tile_cols": buf[2], "region_rows": buf[3]}
+
+
+def denoise_bm3d_noalloc(x: torch.Tensor, sigma: float, out: torch.Tensor | None = None,
+                         stream=None) -> torch.Tensor:
+    """BM3D of each slice of x [Z,H,W] using the library's fixed scratch array
+    (cslsm_denoise_bm3d_noalloc: no device allocation by the library; `out`
+    must be provided by callers that cannot let torch allocate either)."""
+    if x.dim() == 2:
+        x = x[None]
+    Z, H, W = x.shape
+    if out is None:
+        out = torch.empty_like(x)
+    _check(lib().cslsm_denoise_bm3d_noalloc(_dev(x, "x", torch.float32),
+                                            _dev(out, "out", torch.float32, (Z, H, W)), Z, H, W,
+                                            float(sigma), _stream(stream)),
+           "cslsm_denoise_bm3d_noalloc")
+    return out
