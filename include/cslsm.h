@@ -188,6 +188,51 @@ cslsm_status cslsm_bm3d_match(const float *img, int Z, int H, int W, int stage, 
 cslsm_status cslsm_bm3d_stage(int stage, const float *noisy, const float *guide, float *out,
                               int Z, int H, int W, float sigma, void *stream);
 
+/* ---- batched solver --------------------------------------------------------
+ * Many independent measurements (each with its own plan: size, slice count,
+ * patterns) reconstructed by Algorithm 1 with the TV prior (and the z term
+ * when gamma > 0) in one persistent kernel launch, recorded once into a CUDA
+ * graph at creation and replayed by every run.  Per measurement the result
+ * is bit-identical to cslsm_admm_solve with the same parameters and storage
+ * type.  The persistent kernel schedules per-measurement phase chains
+ * (x-update, then the TV u-step of each slice in Gauss-Seidel order) from a
+ * global work counter; each dependency wait is bounded (4 s by default) and a
+ * wait that runs out makes cslsm_batch_wait return CSLSM_ERR_TIMEOUT. */
+typedef struct cslsm_batch_s *cslsm_batch;
+
+typedef struct {
+    cslsm_plan plan; /* geometry, DMD patterns; its state buffers hold u, d */
+    const float *b;  /* device [n_shots][H][W] measurement */
+    float *v_out;    /* device [Z][H][W]: receives v^K */
+} cslsm_batch_item;
+
+/* Create a batch over n_items items (plans on the current device) with one
+ * parameter set: denoiser TV, tol 0, init_user 0, tv_inner <= 24.  b and
+ * v_out pointers are recorded: every run reads and writes the same buffers,
+ * and u^0 = d^0 = 0 in each run.  With cslsm_set_autotune(1) the tile rows
+ * are chosen by timing one-iteration runs of a few candidates (this
+ * synchronises `stream` and overwrites the items' state and v_out).
+ * Synchronises `stream`. */
+cslsm_status cslsm_batch_create(cslsm_batch *batch, const cslsm_batch_item *items, int n_items,
+                                const cslsm_admm_params *params, void *stream);
+
+/* Enqueue one whole batched solve on `stream` (one graph launch). */
+cslsm_status cslsm_batch_run(cslsm_batch batch, void *stream);
+
+/* Synchronise `stream` and report the last run's outcome: CSLSM_OK, or
+ * CSLSM_ERR_TIMEOUT if a bounded device-side wait gave up (every CTA then
+ * stops and the outputs are incomplete). */
+cslsm_status cslsm_batch_wait(cslsm_batch batch, void *stream);
+
+/* Set the wait limit (seconds) of later runs.  test_stall = 1 makes every
+ * dependency wait target a count that never arrives, so that the next run
+ * exercises the time-out path (for tests); 0 restores normal waits.
+ * Synchronises the device. */
+cslsm_status cslsm_batch_set_wait_limit(cslsm_batch batch, double seconds, int test_stall);
+
+/* Release the batch (synchronises the device).  NULL is accepted. */
+cslsm_status cslsm_batch_destroy(cslsm_batch batch);
+
 /* ---- allocation-free BM3D ------------------------------------------------
  * The paper has no counterpart to this entry point; it serves callers that
  * cannot allocate device memory when they denoise (inside a CUDA graph

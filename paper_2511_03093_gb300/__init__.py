@@ -47,6 +47,12 @@ class AdmmParams(ctypes.Structure):
                 ("storage", ctypes.c_int)]
 
 
+class BatchItem(ctypes.Structure):
+    """Mirror of cslsm_batch_item."""
+
+    _fields_ = [("plan", ctypes.c_void_p), ("b", ctypes.c_void_p), ("v_out", ctypes.c_void_p)]
+
+
 class AdmmStats(ctypes.Structure):
     _fields_ = [("iters_done", ctypes.c_int), ("rel_change", ctypes.c_double)]
 
@@ -110,6 +116,16 @@ def lib() -> ctypes.CDLL:
     L.cslsm_last_error.restype = ctypes.c_char_p
     L.cslsm_abi_version.argtypes = []
     L.cslsm_abi_version.restype = I
+    L.cslsm_batch_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(BatchItem), I,
+                                     ctypes.POINTER(AdmmParams), P]
+    L.cslsm_batch_create.restype = I
+    for name in ("cslsm_batch_run", "cslsm_batch_wait"):
+        getattr(L, name).argtypes = [P, P]
+        getattr(L, name).restype = I
+    L.cslsm_batch_set_wait_limit.argtypes = [P, ctypes.c_double, I]
+    L.cslsm_batch_set_wait_limit.restype = I
+    L.cslsm_batch_destroy.argtypes = [P]
+    L.cslsm_batch_destroy.restype = I
     L.cslsm_bm3d_noalloc_capacity.argtypes = []
     L.cslsm_bm3d_noalloc_capacity.restype = ctypes.c_size_t
     L.cslsm_bm3d_scratch_bytes.argtypes = [I, I, I]
@@ -337,3 +353,40 @@ def denoise_bm3d_noalloc(x: torch.Tensor, sigma: float, out: torch.Tensor | None
                                             float(sigma), _stream(stream)),
            "cslsm_denoise_bm3d_noalloc")
     return out
+
+
+class Batch:
+    """Many measurements solved by one persistent launch replayed from a CUDA graph
+    (cslsm_batch_*).  items: list of (Plan, b, v_out) with device tensors."""
+
+    def __init__(self, items, params: Params, stream=None):
+        self._keep = list(items)  # the batch records these tensors' addresses
+        arr = (BatchItem * len(items))()
+        for k, (plan, b, v_out) in enumerate(items):
+            arr[k] = BatchItem(plan._h, _dev(b, "b", torch.float32, plan.meas_shape),
+                               _dev(v_out, "v_out", torch.float32, plan.vol_shape))
+        self._h = ctypes.c_void_p()
+        cp = params.to_c()
+        _check(lib().cslsm_batch_create(ctypes.byref(self._h), arr, len(items), ctypes.byref(cp),
+                                        _stream(stream)), "cslsm_batch_create")
+
+    def run(self, stream=None) -> None:
+        _check(lib().cslsm_batch_run(self._h, _stream(stream)), "cslsm_batch_run")
+
+    def wait(self, stream=None) -> None:
+        _check(lib().cslsm_batch_wait(self._h, _stream(stream)), "cslsm_batch_wait")
+
+    def set_wait_limit(self, seconds: float, test_stall: bool = False) -> None:
+        _check(lib().cslsm_batch_set_wait_limit(self._h, float(seconds), int(test_stall)),
+               "cslsm_batch_set_wait_limit")
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) and self._h.value:
+            _check(lib().cslsm_batch_destroy(self._h), "cslsm_batch_destroy")
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -7,7 +7,10 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <new>
+#include <utility>
+#include <vector>
 
 #include "internal.cuh"
 
@@ -469,6 +472,216 @@ cslsm_status cslsm_denoise(int denoiser, const float *in, float *out, int Z, int
     st = tv_prox_slices(a, pbuf, s);
     if (pbuf) cudaFreeAsync(pbuf, s);
     return st;
+}
+
+}  // extern "C"
+
+struct cslsm_batch_s {
+    int device;
+    BatchRun run;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<std::pair<void *, size_t>> zero;  // state buffers zeroed by each run
+};
+
+namespace {
+
+void free_batch(cslsm_batch_s *b)
+{
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    cudaFree(b->run.mem);
+    delete b;
+}
+
+cslsm_status build_and_capture(cslsm_batch_s *bt, const BatchSpec &spec)
+{
+    cslsm_status st = batch_build(spec, bt->run);
+    if (st) return st;
+    cudaStream_t cs = nullptr;
+    CSLSM_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        for (auto &z : bt->zero)
+            if ((e = cudaMemsetAsync(z.first, 0, z.second, cs)) != cudaSuccess) break;
+        if (e == cudaSuccess) st = batch_enqueue(bt->run, cs);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+        if (e == cudaSuccess) e = e2;
+        bt->graph = g;
+    }
+    if (e == cudaSuccess && !st) e = cudaGraphInstantiate(&bt->exec, bt->graph, 0);
+    cudaStreamDestroy(cs);
+    if (st) return st;
+    if (e != cudaSuccess) {
+        set_error("batch graph capture: %s", cudaGetErrorString(e));
+        return CSLSM_ERR_CUDA;
+    }
+    return CSLSM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+cslsm_status cslsm_batch_create(cslsm_batch *out, const cslsm_batch_item *items, int n_items,
+                                const cslsm_admm_params *prm, void *stream)
+{
+    CHECK_ARG(out != nullptr, "batch output pointer is NULL");
+    *out = nullptr;
+    CHECK_ARG(items != nullptr && n_items >= 1, "need at least one item");
+    cslsm_status st = check_params(prm, false);
+    if (st) return st;
+    CHECK_ARG(prm->denoiser == CSLSM_DEN_TV, "the batched solver runs the TV prior");
+    CHECK_ARG(prm->tol == 0.f, "the batched solver runs a fixed iteration count (tol = 0)");
+    CHECK_ARG(prm->init_user == 0, "the batched solver starts from u = d = 0");
+    CHECK_ARG(prm->iters >= 1, "iters must be >= 1");
+    if (prm->tv_inner > tv_max_steps_per_launch()) {
+        set_error("the batched solver runs at most %d TV steps per prox",
+                  tv_max_steps_per_launch());
+        return CSLSM_ERR_UNSUPPORTED;
+    }
+    int dev = 0;
+    for (int i = 0; i < n_items; ++i) {
+        CHECK_ARG(items[i].plan && items[i].b && items[i].v_out, "item %d is incomplete", i);
+        if (i == 0) dev = items[i].plan->device;
+        CHECK_ARG(items[i].plan->device == dev, "items on different devices");
+    }
+    int cur = -1;
+    CSLSM_CUDA(cudaGetDevice(&cur));
+    CHECK_ARG(cur == dev, "the items' plans belong to device %d, current device is %d", dev, cur);
+    cudaStream_t s = as_stream(stream);
+    CSLSM_CUDA(cudaStreamSynchronize(s));
+    cslsm_batch_s *bt = new (std::nothrow) cslsm_batch_s();
+    CHECK_ARG(bt != nullptr, "host allocation failed");
+    bt->device = dev;
+    const int T = prm->lambda > 0.f ? prm->tv_inner : 0;
+    BatchSpec spec;
+    spec.iters = prm->iters;
+    spec.T = prm->tv_inner;
+    spec.storage = prm->storage;
+    spec.stall_test = 0;
+    spec.rho = prm->rho;
+    spec.lam = prm->lambda;
+    spec.gamma = prm->gamma;
+    spec.tau = prm->tv_tau;
+    spec.wait_limit_s = 4.0;
+    const size_t esz = prm->storage == CSLSM_STORE_FP32 ? 4 : 2;
+    int maxH = 1;
+    for (int i = 0; i < n_items; ++i) {
+        const cslsm_plan_s *p = items[i].plan;
+        BatchItemSpec it{};
+        it.u = p->u;
+        it.d = p->d;
+        it.w = p->w;
+        it.b = items[i].b;
+        it.v_out = items[i].v_out;
+        it.words = p->words;
+        it.wstride = p->nsets > 1 ? p->g.HW() : 0;
+        it.H = p->g.H;
+        it.W = p->g.W;
+        it.N = p->g.N;
+        it.R = p->g.R;
+        spec.items.push_back(it);
+        bt->zero.push_back({p->u, esz * (size_t)p->g.voxels()});
+        bt->zero.push_back({p->d, esz * (size_t)p->g.voxels()});
+        maxH = std::max(maxH, p->g.H);
+    }
+    // tile rows: the largest region that fits (least halo work) unless timing
+    // a few candidates on the batch itself is asked for (autotune mode 1)
+    const int rows_max = std::max(2, std::min(batch_max_tile_rows(T), maxH));
+    int rows = rows_max;
+    if (tv_get_mode() == 1) {
+        float best = 1e30f;
+        const int cand[] = {rows_max, 32, 24, 16};
+        for (int c : cand) {
+            if (c > rows_max) continue;
+            BatchSpec trial = spec;
+            trial.iters = 1;
+            for (auto &it : trial.items) it.TH = c;
+            cslsm_batch_s probe;
+            probe.device = dev;
+            probe.zero = bt->zero;
+            st = batch_build(trial, probe.run);
+            float ms = 1e30f;
+            if (!st) {
+                cudaEvent_t e0, e1;
+                cudaEventCreate(&e0);
+                cudaEventCreate(&e1);
+                for (auto &z : probe.zero) cudaMemsetAsync(z.first, 0, z.second, s);
+                cudaEventRecord(e0, s);
+                st = batch_enqueue(probe.run, s);
+                cudaEventRecord(e1, s);
+                if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1))
+                    ms = 1e30f;
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+            }
+            cudaFree(probe.run.mem);
+            probe.run.mem = nullptr;
+            if (st) {
+                free_batch(bt);
+                return st;
+            }
+            if (ms < best) {
+                best = ms;
+                rows = c;
+            }
+        }
+    }
+    for (auto &it : spec.items) it.TH = rows;
+    st = build_and_capture(bt, spec);
+    if (st) {
+        free_batch(bt);
+        return st;
+    }
+    *out = bt;
+    return CSLSM_OK;
+}
+
+cslsm_status cslsm_batch_run(cslsm_batch batch, void *stream)
+{
+    CHECK_ARG(batch != nullptr, "batch is NULL");
+    int cur = -1;
+    CSLSM_CUDA(cudaGetDevice(&cur));
+    CHECK_ARG(cur == batch->device, "batch belongs to device %d", batch->device);
+    LaunchScope ls(K_BATCH, as_stream(stream));
+    CSLSM_CUDA(cudaGraphLaunch(batch->exec, as_stream(stream)));
+    return CSLSM_OK;
+}
+
+cslsm_status cslsm_batch_wait(cslsm_batch batch, void *stream)
+{
+    CHECK_ARG(batch != nullptr, "batch is NULL");
+    CSLSM_CUDA(cudaStreamSynchronize(as_stream(stream)));
+    int err = 0;
+    CSLSM_CUDA(cudaMemcpy(&err, batch->run.error, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) {
+        set_error("a device-side wait of the batched solver ran out of time");
+        return CSLSM_ERR_TIMEOUT;
+    }
+    return CSLSM_OK;
+}
+
+cslsm_status cslsm_batch_set_wait_limit(cslsm_batch batch, double seconds, int test_stall)
+{
+    CHECK_ARG(batch != nullptr, "batch is NULL");
+    CHECK_ARG(seconds > 0.0 && seconds <= 600.0, "seconds must be in (0, 600]");
+    CHECK_ARG(test_stall == 0 || test_stall == 1, "test_stall must be 0 or 1");
+    CSLSM_CUDA(cudaDeviceSynchronize());
+    return batch_set_wait(batch->run, seconds, test_stall);
+}
+
+cslsm_status cslsm_batch_destroy(cslsm_batch batch)
+{
+    if (!batch) return CSLSM_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    free_batch(batch);
+    if (e != cudaSuccess) {
+        set_error("batch_destroy: %s", cudaGetErrorString(e));
+        return CSLSM_ERR_CUDA;
+    }
+    return CSLSM_OK;
 }
 
 cslsm_status cslsm_set_autotune(int mode)

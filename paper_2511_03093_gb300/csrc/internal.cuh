@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "cslsm.h"
 
 namespace cslsm {
@@ -28,7 +30,7 @@ void set_error(const char *fmt, ...);
 // Kernels of the library, for launch accounting and sampled timing (timing.cu).
 enum KernelId {
     K_PACK = 0, K_FORWARD, K_ADJOINT, K_XUPDATE, K_TIK_ITER, K_TIK_PROX, K_TV_TILE, K_PSNR,
-    K_REDUCE, K_BM3D_PREP, K_BM3D_MATCH, K_BM3D_FILTER, K_BM3D_FINISH, K_COUNT
+    K_REDUCE, K_BM3D_PREP, K_BM3D_MATCH, K_BM3D_FILTER, K_BM3D_FINISH, K_BATCH, K_COUNT
 };
 
 // Wrap every kernel launch: counts it and, when timing is on, records CUDA
@@ -116,6 +118,7 @@ int tv_max_steps_per_launch();
 // launch of every shape key (outside stream capture) and keep the fastest;
 // 2 + k: force variant k (tests).
 void tv_set_mode(int mode);
+int tv_get_mode();
 // The shape (variant, TH, TW, RH) a launch of this geometry would use now.
 cslsm_status tv_query_shape(int H, int W, int T, int nslices, int *out4);
 
@@ -138,5 +141,36 @@ cslsm_status bm3d_stage_only(int stage, const float *noisy, const float *guide, 
                              int nslices, int H, int W, float sigma, void *ws, cudaStream_t s);
 cslsm_status bm3d_match_only(const float *img, int nslices, int H, int W, int stage, int *lists,
                              int *counts, void *ws, cudaStream_t s);
+
+// ---- persistent batched solver (kernels_batch.cu) ------------------------------
+struct BatchItemSpec {
+    void *u, *d, *w;  // state and workspace of the item's plan (storage type)
+    const float *b;
+    float *v_out;
+    const uint32_t *words;
+    int wstride;
+    int H, W, N, R;
+    int TH;           // TV tile rows (tile columns follow from the steps)
+};
+struct BatchSpec {
+    std::vector<BatchItemSpec> items;
+    int iters, T, storage, stall_test;
+    float rho, lam, gamma, tau;
+    double wait_limit_s;
+};
+struct BatchRun {
+    void *mem = nullptr;     // one device allocation (descriptors, tables, counters)
+    void *desc = nullptr;
+    void *counters = nullptr;
+    size_t counters_bytes = 0;
+    int *error = nullptr;
+    size_t smem = 0;
+    int grid = 0, storage = 0;
+};
+int batch_max_tile_rows(int T);
+cslsm_status batch_build(const BatchSpec &spec, BatchRun &run);
+cslsm_status batch_set_wait(const BatchRun &run, double limit_s, int stall_test);
+// Enqueues the counter reset and the persistent launch (no state reset).
+cslsm_status batch_enqueue(const BatchRun &run, cudaStream_t s);
 
 }  // namespace cslsm

@@ -27,6 +27,26 @@ __device__ __forceinline__ float ld<__half>(const __half *p)
     return __half2float(*p);
 }
 
+// Loads that bypass L1 (cached in L2 only): safe for data another SM wrote
+// earlier in the same kernel (the persistent batched solver).
+template <typename S>
+__device__ __forceinline__ float ld_l2(const S *p);
+template <>
+__device__ __forceinline__ float ld_l2<float>(const float *p)
+{
+    return __ldcg(p);
+}
+template <>
+__device__ __forceinline__ float ld_l2<__nv_bfloat16>(const __nv_bfloat16 *p)
+{
+    return __bfloat162float(__ldcg(p));
+}
+template <>
+__device__ __forceinline__ float ld_l2<__half>(const __half *p)
+{
+    return __half2float(__ldcg(p));
+}
+
 template <typename S>
 __device__ __forceinline__ void st(S *p, float v);
 template <>

@@ -19,7 +19,8 @@ namespace {
 const char *const kNames[K_COUNT] = {"pack_masks", "forward",  "adjoint",      "xupdate_w",
                                      "tikhonov_iter", "tikhonov_prox", "tv_tile",
                                      "psnr_partials", "reduce_finish", "bm3d_prep",
-                                     "bm3d_match", "bm3d_filter", "bm3d_finish"};
+                                     "bm3d_match", "bm3d_filter", "bm3d_finish",
+                                     "batch_persistent"};
 
 struct Rec {
     int kernel;

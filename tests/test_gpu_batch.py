@@ -1,0 +1,106 @@
+"""Batched solver: one persistent launch under a CUDA graph over measurements of
+uneven size and slice count.  Per measurement it must reproduce the plain
+per-volume solve bit for bit (same FP32 / BF16 arithmetic, tiling does not
+change any pixel's operations), replay identically, and report a device-side
+wait that runs out as CSLSM_ERR_TIMEOUT without hanging."""
+import numpy as np
+import pytest
+
+import synth
+from tests.gpu_util import to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cs():
+    import torch
+
+    from paper_2511_03093_gb300 import build as b
+
+    b.build()
+    import paper_2511_03093_gb300 as m
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return m
+
+
+SIZES = [(8, 64, 64), (16, 96, 80), (4, 130, 101), (8, 40, 200), (1, 33, 47)]
+
+
+def _items(cs, seed0):
+    import torch
+
+    items, plans = [], []
+    for k, (Z, H, W) in enumerate(SIZES):
+        w = synth.Workload(f"b{k}", Z, H, W, drift=True, mask_p=0.3, peak=50.0, sigma_g=0.02,
+                           seed=seed0 + k, n_blobs=max(4, Z * H * W // 400))
+        data = synth.generate(w)
+        plan = cs.Plan(H, W, 1, Z, to_dev(data["masks"]))
+        b = to_dev(data["b"])
+        v = torch.empty((Z, H, W), dtype=torch.float32, device="cuda")
+        items.append((plan, b, v))
+    return items
+
+
+@pytest.mark.parametrize("gamma,storage", [(0.2, "fp32"), (0.0, "fp32"), (0.2, "bf16")])
+def test_batch_equals_per_volume(cs, gamma, storage):
+    import torch
+
+    items = _items(cs, 500)
+    prm = cs.Params(rho=1.0, lam=0.05, gamma=gamma, iters=12, denoiser="tv", tv_inner=20,
+                    storage=storage)
+    batch = cs.Batch(items, prm)
+    batch.run()
+    batch.wait()
+    got = [to_np(v).copy() for _, _, v in items]
+    batch.run()  # graph replay
+    batch.wait()
+    for (plan, b, v), g in zip(items, got):
+        np.testing.assert_array_equal(to_np(v), g)
+        ref = plan.solve(b, prm)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(g, to_np(ref))
+    batch.close()
+
+
+def test_batch_autotuned_tiles(cs):
+    import torch
+
+    items = _items(cs, 600)
+    prm = cs.Params(rho=1.0, lam=0.05, gamma=0.2, iters=5, denoiser="tv", tv_inner=20)
+    try:
+        cs.set_autotune(1)
+        batch = cs.Batch(items, prm)
+    finally:
+        cs.set_autotune(0)
+    batch.run()
+    batch.wait()
+    for plan, b, v in items:
+        ref = plan.solve(b, prm)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(to_np(v), to_np(ref))
+    batch.close()
+
+
+def test_batch_wait_timeout_is_reported(cs):
+    items = _items(cs, 700)[:2]
+    prm = cs.Params(rho=1.0, lam=0.05, gamma=0.2, iters=3, denoiser="tv", tv_inner=10)
+    batch = cs.Batch(items, prm)
+    batch.set_wait_limit(0.05, test_stall=True)
+    batch.run()
+    with pytest.raises(cs.CslsmError) as ei:
+        batch.wait()
+    assert ei.value.status == 3  # CSLSM_ERR_TIMEOUT
+    batch.set_wait_limit(4.0, test_stall=False)
+    batch.run()
+    batch.wait()  # the context is still usable and a normal run completes
+    batch.close()
+
+
+def test_batch_rejects_unsupported(cs):
+    items = _items(cs, 800)[:1]
+    for prm in (cs.Params(denoiser="bm3d"), cs.Params(denoiser="tv", tol=1e-3),
+                cs.Params(denoiser="tv", tv_inner=30)):
+        with pytest.raises(cs.CslsmError):
+            cs.Batch(items, prm)
