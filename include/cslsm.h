@@ -233,6 +233,43 @@ cslsm_status cslsm_batch_set_wait_limit(cslsm_batch batch, double seconds, int t
 /* Release the batch (synchronises the device).  NULL is accepted. */
 cslsm_status cslsm_batch_destroy(cslsm_batch batch);
 
+/* ---- differentiable unrolled solver ----------------------------------------
+ * K iterations of Algorithm 1 unrolled into a differentiable map, for learning
+ * the DMD patterns and the parameters (rho, lambda, gamma) end to end.  The
+ * paper's method with two relaxations: the binary patterns become
+ * m = sigmoid(logits) (continuous, D = sum_r m_r^2 in the Woodbury x-update),
+ * and TV becomes the Huber-smoothed TV (|x| - eps/2 beyond eps, |x|^2/(2 eps)
+ * below), whose prox is taken by tv_steps projected-gradient steps on its
+ * dual from p = 0: q = div p - h/theta, a = p + tau (grad q - (eps/theta) p),
+ * p <- a / max(1, |a|), u = h - theta div p; h is the Gauss-Seidel input of
+ * Eq. (u-update), theta = lambda / (rho + 2 gamma).  One shot per volume
+ * (R = Z), u^0 = d^0 = 0, output v^K.
+ * Layouts: logits, v_out, logits_bar [B][Z][H][W]; b [B][H][W]; ckpt holds
+ * ceil(iters / ckpt_every) checkpoints of (u, d): [n_ckpt][2][B][Z][H][W]
+ * floats; ws is caller-owned device scratch of cslsm_unrolled_workspace_bytes
+ * bytes.  The backward recomputes each checkpoint segment and runs the
+ * hand-written adjoint; it synchronises `stream` (to combine the scalar
+ * gradients) and writes dL/dlogits and scalar_bar (device double[3]) =
+ * {dL/drho, dL/dlambda, dL/dgamma} for the given v_bar = dL/dv^K. */
+typedef struct {
+    float rho, lambda, gamma; /* rho > 0, lambda > 0, gamma >= 0 */
+    int iters;                /* K */
+    int tv_steps;             /* dual steps per prox */
+    float tv_tau;             /* dual step, (0, 1/8] */
+    float huber_eps;          /* >= 0 (0: plain TV) */
+    int ckpt_every;           /* checkpoint period in iterations */
+} cslsm_unrolled_params;
+
+size_t cslsm_unrolled_workspace_bytes(int B, int Z, int H, int W,
+                                      const cslsm_unrolled_params *params);
+cslsm_status cslsm_unrolled_forward(const float *logits, const float *b, int B, int Z, int H,
+                                    int W, const cslsm_unrolled_params *params, float *v_out,
+                                    float *ckpt, void *ws, void *stream);
+cslsm_status cslsm_unrolled_backward(const float *logits, const float *b, int B, int Z, int H,
+                                     int W, const cslsm_unrolled_params *params,
+                                     const float *ckpt, const float *v_bar, float *logits_bar,
+                                     double *scalar_bar, void *ws, void *stream);
+
 /* ---- allocation-free BM3D ------------------------------------------------
  * The paper has no counterpart to this entry point; it serves callers that
  * cannot allocate device memory when they denoise (inside a CUDA graph

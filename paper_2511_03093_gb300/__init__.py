@@ -53,6 +53,14 @@ class BatchItem(ctypes.Structure):
     _fields_ = [("plan", ctypes.c_void_p), ("b", ctypes.c_void_p), ("v_out", ctypes.c_void_p)]
 
 
+class UnrolledParams(ctypes.Structure):
+    """Mirror of cslsm_unrolled_params."""
+
+    _fields_ = [("rho", ctypes.c_float), ("lambda_", ctypes.c_float), ("gamma", ctypes.c_float),
+                ("iters", ctypes.c_int), ("tv_steps", ctypes.c_int), ("tv_tau", ctypes.c_float),
+                ("huber_eps", ctypes.c_float), ("ckpt_every", ctypes.c_int)]
+
+
 class AdmmStats(ctypes.Structure):
     _fields_ = [("iters_done", ctypes.c_int), ("rel_change", ctypes.c_double)]
 
@@ -126,6 +134,14 @@ def lib() -> ctypes.CDLL:
     L.cslsm_batch_set_wait_limit.restype = I
     L.cslsm_batch_destroy.argtypes = [P]
     L.cslsm_batch_destroy.restype = I
+    L.cslsm_unrolled_workspace_bytes.argtypes = [I, I, I, I, ctypes.POINTER(UnrolledParams)]
+    L.cslsm_unrolled_workspace_bytes.restype = ctypes.c_size_t
+    L.cslsm_unrolled_forward.argtypes = [P, P, I, I, I, I, ctypes.POINTER(UnrolledParams), P, P,
+                                         P, P]
+    L.cslsm_unrolled_forward.restype = I
+    L.cslsm_unrolled_backward.argtypes = [P, P, I, I, I, I, ctypes.POINTER(UnrolledParams), P, P,
+                                          P, P, P, P]
+    L.cslsm_unrolled_backward.restype = I
     L.cslsm_bm3d_noalloc_capacity.argtypes = []
     L.cslsm_bm3d_noalloc_capacity.restype = ctypes.c_size_t
     L.cslsm_bm3d_scratch_bytes.argtypes = [I, I, I]
@@ -390,3 +406,63 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def _unrolled_params(rho, lam, gamma, cfg) -> UnrolledParams:
+    return UnrolledParams(float(rho), float(lam), float(gamma), int(cfg["iters"]),
+                          int(cfg["tv_steps"]), float(cfg["tv_tau"]), float(cfg["huber_eps"]),
+                          int(cfg["ckpt_every"]))
+
+
+class _UnrolledADMM(torch.autograd.Function):
+    """v^K of the unrolled, relaxed PnP-ADMM (cslsm_unrolled_forward); its backward is
+    the library's hand-written adjoint (cslsm_unrolled_backward)."""
+
+    @staticmethod
+    def forward(ctx, logits, b, rho, lam, gamma, cfg):
+        B, Z, H, W = logits.shape
+        cp = _unrolled_params(rho.item(), lam.item(), gamma.item(), cfg)
+        nbytes = lib().cslsm_unrolled_workspace_bytes(B, Z, H, W, ctypes.byref(cp))
+        if nbytes == 0:
+            raise ValueError("invalid unrolled-solver parameters or sizes")
+        ws = torch.empty(nbytes, dtype=torch.uint8, device=logits.device)
+        nck = -(-cfg["iters"] // cfg["ckpt_every"])
+        ckpt = torch.empty((nck, 2, B, Z, H, W), dtype=torch.float32, device=logits.device)
+        v = torch.empty_like(logits)
+        _check(lib().cslsm_unrolled_forward(_dev(logits, "logits", torch.float32),
+                                            _dev(b, "b", torch.float32, (B, H, W)), B, Z, H, W,
+                                            ctypes.byref(cp), _dev(v, "v", torch.float32),
+                                            _dev(ckpt, "ckpt", torch.float32),
+                                            ctypes.c_void_p(ws.data_ptr()), _stream()),
+               "cslsm_unrolled_forward")
+        ctx.save_for_backward(logits, b, ckpt)
+        ctx.ws, ctx.cp = ws, cp
+        return v
+
+    @staticmethod
+    def backward(ctx, vbar):
+        logits, b, ckpt = ctx.saved_tensors
+        B, Z, H, W = logits.shape
+        vbar = vbar.contiguous().float()
+        lbar = torch.empty_like(logits)
+        sbar = torch.empty(3, dtype=torch.float64, device=logits.device)
+        _check(lib().cslsm_unrolled_backward(_dev(logits, "logits", torch.float32),
+                                             _dev(b, "b", torch.float32), B, Z, H, W,
+                                             ctypes.byref(ctx.cp), _dev(ckpt, "ckpt", torch.float32),
+                                             _dev(vbar, "vbar", torch.float32),
+                                             _dev(lbar, "lbar", torch.float32),
+                                             ctypes.c_void_p(sbar.data_ptr()),
+                                             ctypes.c_void_p(ctx.ws.data_ptr()), _stream()),
+               "cslsm_unrolled_backward")
+        s = sbar.to(torch.float32)
+        return lbar, None, s[0], s[1], s[2], None
+
+
+def unrolled_admm(logits: torch.Tensor, b: torch.Tensor, rho: torch.Tensor, lam: torch.Tensor,
+                  gamma: torch.Tensor, iters: int = 30, tv_steps: int = 20, tv_tau: float = 0.125,
+                  huber_eps: float = 1e-3, ckpt_every: int = 5) -> torch.Tensor:
+    """Differentiable v^K of the unrolled PnP-ADMM with relaxed masks sigmoid(logits)
+    [B,Z,H,W] and Huber-TV + z prior; b [B,H,W]; rho, lam, gamma 0-dim tensors."""
+    cfg = dict(iters=iters, tv_steps=tv_steps, tv_tau=tv_tau, huber_eps=huber_eps,
+               ckpt_every=ckpt_every)
+    return _UnrolledADMM.apply(logits, b, rho, lam, gamma, cfg)

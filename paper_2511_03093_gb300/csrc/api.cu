@@ -684,6 +684,56 @@ cslsm_status cslsm_batch_destroy(cslsm_batch batch)
     return CSLSM_OK;
 }
 
+namespace {
+cslsm_status check_unrolled(int B, int Z, int H, int W, const cslsm_unrolled_params *p)
+{
+    CHECK_ARG(p != nullptr, "params is NULL");
+    CHECK_ARG(B >= 1 && Z >= 1 && H >= 1 && W >= 1, "B, Z, H, W must be >= 1");
+    CHECK_ARG((long long)B * Z * H * W < (1ll << 31), "B*Z*H*W must be < 2^31");
+    CHECK_ARG(std::isfinite(p->rho) && p->rho > 0.f, "rho must be > 0");
+    CHECK_ARG(std::isfinite(p->lambda) && p->lambda > 0.f, "lambda must be > 0");
+    CHECK_ARG(std::isfinite(p->gamma) && p->gamma >= 0.f, "gamma must be >= 0");
+    CHECK_ARG(p->iters >= 1 && p->tv_steps >= 1 && p->ckpt_every >= 1,
+              "iters, tv_steps, ckpt_every must be >= 1");
+    CHECK_ARG(std::isfinite(p->tv_tau) && p->tv_tau > 0.f && p->tv_tau <= 0.125f,
+              "tv_tau must be in (0, 1/8]");
+    CHECK_ARG(std::isfinite(p->huber_eps) && p->huber_eps >= 0.f, "huber_eps must be >= 0");
+    return CSLSM_OK;
+}
+}  // namespace
+
+size_t cslsm_unrolled_workspace_bytes(int B, int Z, int H, int W, const cslsm_unrolled_params *p)
+{
+    if (check_unrolled(B, Z, H, W, p)) return 0;
+    return unrolled_workspace_bytes(B, Z, H, W, p->tv_steps, p->ckpt_every);
+}
+
+cslsm_status cslsm_unrolled_forward(const float *logits, const float *b, int B, int Z, int H,
+                                    int W, const cslsm_unrolled_params *p, float *v_out,
+                                    float *ckpt, void *ws, void *stream)
+{
+    cslsm_status st = check_unrolled(B, Z, H, W, p);
+    if (st) return st;
+    CHECK_ARG(logits && b && v_out && ckpt && ws, "logits, b, v_out, ckpt, ws must be non-NULL");
+    return unrolled_forward(B, Z, H, W, p->rho, p->lambda, p->gamma, p->iters, p->tv_steps,
+                            p->tv_tau, p->huber_eps, p->ckpt_every, logits, b, v_out, ckpt, ws,
+                            as_stream(stream));
+}
+
+cslsm_status cslsm_unrolled_backward(const float *logits, const float *b, int B, int Z, int H,
+                                     int W, const cslsm_unrolled_params *p, const float *ckpt,
+                                     const float *v_bar, float *logits_bar, double *scalar_bar,
+                                     void *ws, void *stream)
+{
+    cslsm_status st = check_unrolled(B, Z, H, W, p);
+    if (st) return st;
+    CHECK_ARG(logits && b && ckpt && v_bar && logits_bar && scalar_bar && ws,
+              "every pointer must be non-NULL");
+    return unrolled_backward(B, Z, H, W, p->rho, p->lambda, p->gamma, p->iters, p->tv_steps,
+                             p->tv_tau, p->huber_eps, p->ckpt_every, logits, b, ckpt, v_bar,
+                             logits_bar, scalar_bar, ws, as_stream(stream));
+}
+
 cslsm_status cslsm_set_autotune(int mode)
 {
     CHECK_ARG(mode >= 0 && mode <= 5, "autotune mode must be in [0, 5]");

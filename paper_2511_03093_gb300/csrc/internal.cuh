@@ -30,7 +30,7 @@ void set_error(const char *fmt, ...);
 // Kernels of the library, for launch accounting and sampled timing (timing.cu).
 enum KernelId {
     K_PACK = 0, K_FORWARD, K_ADJOINT, K_XUPDATE, K_TIK_ITER, K_TIK_PROX, K_TV_TILE, K_PSNR,
-    K_REDUCE, K_BM3D_PREP, K_BM3D_MATCH, K_BM3D_FILTER, K_BM3D_FINISH, K_BATCH, K_COUNT
+    K_REDUCE, K_BM3D_PREP, K_BM3D_MATCH, K_BM3D_FILTER, K_BM3D_FINISH, K_BATCH, K_DIFF, K_COUNT
 };
 
 // Wrap every kernel launch: counts it and, when timing is on, records CUDA
@@ -168,6 +168,16 @@ struct BatchRun {
     int grid = 0, storage = 0;
 };
 int batch_max_tile_rows(int T);
+
+// ---- differentiable unrolled solver (kernels_diff.cu) -------------------------
+size_t unrolled_workspace_bytes(int B, int Z, int H, int W, int T, int S);
+cslsm_status unrolled_forward(int B, int Z, int H, int W, float rho, float lam, float gam,
+                              int K, int T, float tau, float eps, int S, const float *logits,
+                              const float *b, float *vout, float *ckpt, void *ws, cudaStream_t s);
+cslsm_status unrolled_backward(int B, int Z, int H, int W, float rho, float lam, float gam,
+                               int K, int T, float tau, float eps, int S, const float *logits,
+                               const float *b, const float *ckpt, const float *vbar,
+                               float *logits_bar, double *scal_bar, void *ws, cudaStream_t s);
 cslsm_status batch_build(const BatchSpec &spec, BatchRun &run);
 cslsm_status batch_set_wait(const BatchRun &run, double limit_s, int stall_test);
 // Enqueues the counter reset and the persistent launch (no state reset).

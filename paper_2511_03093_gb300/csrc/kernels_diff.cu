@@ -1,0 +1,588 @@
+// Differentiable unrolled PnP-ADMM (relaxed DMD masks, Huber-smoothed TV with
+// the z-smoothness Gauss-Seidel sweep) and its hand-written reverse pass.
+//
+// Forward, K iterations of Algorithm 1 on a batch of B volumes [Z][H][W]
+// (one shot, R = Z), from u = d = 0:
+//   m     = sigmoid(logits)                             relaxed DMD patterns
+//   x-update (Eq. v-update, Woodbury with D = sum_r m_r^2):
+//         g = u - d,  e = (b - sum_r m_r g_r) / (rho + D),  v_r = g_r + m_r e,
+//         w = v + d
+//   u-step, n = 0..Z-1 in order (Eq. u-update, newest neighbours, cyclic):
+//         h_n = (rho w_n + gamma (u_{n-1} + u_{n+1})) / (rho + 2 gamma)
+//         u_n = prox of theta * HuberTV_eps at h_n, theta = lambda/(rho+2gamma),
+//               by T steps of projected gradient on its dual from p = 0:
+//               q = div p - h/theta,  a = p + tau (grad q - kappa p),
+//               p <- a / max(1, |a|),  kappa = eps / theta,
+//               u_n = h - theta div p
+//   d = w - u.
+// The Huber function |x| - eps/2 (|x| > eps), |x|^2/(2 eps) (|x| <= eps) has the
+// conjugate eps/2 |p|^2 on |p| <= 1, which is the -kappa p damping above.
+// grad: forward differences, zero on the last row / column; div = -grad^T.
+//
+// Reverse.  The caller gives vbar = dL/dv^K.  The state (u^k, d^k) is stored
+// every `ckpt_every` iterations by the forward; the reverse walks the
+// segments backwards, recomputes each segment's states from its checkpoint,
+// and backpropagates one iteration at a time: the dual update, the
+// Gauss-Seidel sweep in reverse slice order (each prox recomputes its T dual
+// iterates and runs their adjoint), the x-update.  Gradients: dL/dlogits and
+// the three scalars dL/drho, dL/dlambda, dL/dgamma (FP64 accumulators).
+//
+// Kernels are plain one-thread-per-pixel passes (a block row of the grid per
+// batch item); the stencils read their neighbours from global memory (L1/L2).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <utility>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace cslsm {
+namespace {
+
+constexpr int kT = 256;
+
+struct Geo {
+    int B, Z, H, W;
+    __host__ __device__ size_t HW() const { return (size_t)H * W; }
+    __host__ __device__ size_t NV() const { return (size_t)Z * H * W; }  // per batch item
+};
+
+__device__ __forceinline__ float sigm(float x) { return 1.f / (1.f + expf(-x)); }
+
+// div of a dual field (components along rows p1, along columns p2) with the
+// Neumann boundary of the forward differences.
+__device__ __forceinline__ float divp(const float *p1, const float *p2, int i, int j, int H, int W)
+{
+    const size_t o = (size_t)i * W + j;
+    const float a = (i < H - 1 ? p1[o] : 0.f) - (i > 0 ? p1[o - W] : 0.f);
+    const float c = (j < W - 1 ? p2[o] : 0.f) - (j > 0 ? p2[o - 1] : 0.f);
+    return a + c;
+}
+
+// ---- x-update ----------------------------------------------------------------
+__global__ void ux_fwd_kernel(const float *__restrict__ U, const float *__restrict__ Dl,
+                              const float *__restrict__ logits, const float *__restrict__ b,
+                              Geo g, float rho, float *__restrict__ Wb, float *__restrict__ vout)
+{
+    const size_t p = blockIdx.x * (size_t)kT + threadIdx.x;
+    const int bi = blockIdx.y;
+    if (p >= g.HW()) return;
+    const size_t base = bi * g.NV() + p, HW = g.HW();
+    float s = 0.f, D = 0.f;
+    for (int r = 0; r < g.Z; ++r) {
+        const size_t o = base + r * HW;
+        const float m = sigm(logits[o]);
+        s += m * (U[o] - Dl[o]);
+        D += m * m;
+    }
+    const float e = (b[bi * HW + p] - s) / (rho + D);
+    for (int r = 0; r < g.Z; ++r) {
+        const size_t o = base + r * HW;
+        const float m = sigm(logits[o]);
+        const float v = (U[o] - Dl[o]) + m * e;
+        Wb[o] = v + Dl[o];
+        if (vout) vout[o] = v;
+    }
+}
+
+// Reverse of ux_fwd: given vbar (may be null) and wbar = dL/dw, accumulates
+// dL/du^k into Uold_bar, writes dL/dd^k into Dbar, adds dL/dlogits into
+// lbar, and dL/drho (direct) into acc[0].
+__global__ void ux_bwd_kernel(const float *__restrict__ U, const float *__restrict__ Dl,
+                              const float *__restrict__ logits, const float *__restrict__ b,
+                              Geo g, float rho, const float *__restrict__ vbar,
+                              const float *__restrict__ Wbar, float *__restrict__ Uold_bar,
+                              float *__restrict__ Dbar, float *__restrict__ lbar,
+                              double *__restrict__ acc)
+{
+    const size_t p = blockIdx.x * (size_t)kT + threadIdx.x;
+    const int bi = blockIdx.y;
+    double rho_bar = 0.0;
+    if (p < g.HW()) {
+        const size_t base = bi * g.NV() + p, HW = g.HW();
+        float s = 0.f, D = 0.f, ebar = 0.f;
+        for (int r = 0; r < g.Z; ++r) {
+            const size_t o = base + r * HW;
+            const float m = sigm(logits[o]);
+            s += m * (U[o] - Dl[o]);
+            D += m * m;
+            const float vb = Wbar[o] + (vbar ? vbar[o] : 0.f);  // v feeds w = v + d and v^K
+            ebar += m * vb;
+        }
+        const float den = rho + D;
+        const float e = (b[bi * HW + p] - s) / den;
+        const float sbar = -ebar / den;
+        const float Dbarv = -ebar * e / den;
+        rho_bar = (double)(-ebar * e / den);
+        for (int r = 0; r < g.Z; ++r) {
+            const size_t o = base + r * HW;
+            const float m = sigm(logits[o]);
+            const float gr = U[o] - Dl[o];
+            const float vb = Wbar[o] + (vbar ? vbar[o] : 0.f);
+            const float gbar = vb + sbar * m;
+            const float mbar = e * vb + sbar * gr + 2.f * m * Dbarv;
+            Uold_bar[o] += gbar;
+            Dbar[o] = Wbar[o] - gbar;
+            lbar[o] += mbar * m * (1.f - m);
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) rho_bar += __shfl_down_sync(0xffffffffu, rho_bar, off);
+    if ((threadIdx.x & 31) == 0) atomicAdd(acc, rho_bar);
+}
+
+// ---- u-step: g formation -----------------------------------------------------
+// h = (rho w_n + gamma (A + C)) / (rho + 2 gamma), A, C the neighbour slices.
+__global__ void hform_kernel(const float *__restrict__ Wn, const float *A, const float *C, Geo g,
+                             float rho, float gam,
+                             float *__restrict__ Hb)
+{
+    const size_t p = blockIdx.x * (size_t)kT + threadIdx.x;
+    const int bi = blockIdx.y;
+    if (p >= g.HW()) return;
+    const size_t o = bi * g.NV() + p;
+    const float s = gam > 0.f ? A[o] + C[o] : 0.f;
+    Hb[bi * g.HW() + p] = (rho * Wn[o] + gam * s) / (rho + 2.f * gam);
+}
+
+// Reverse of hform: hbar -> w_n, neighbours; direct dL/drho, dL/dgamma.
+__global__ void hform_bwd_kernel(const float *__restrict__ Hbar, const float *__restrict__ Wn,
+                                 const float *A, const float *C, Geo g,
+                                 float rho, float gam, float *__restrict__ Wn_bar,
+                                 float *A_bar, float *C_bar,  // may be the same slice (Z = 2)
+                                 double *__restrict__ acc)
+{
+    const size_t p = blockIdx.x * (size_t)kT + threadIdx.x;
+    const int bi = blockIdx.y;
+    double rb = 0.0, gb = 0.0;
+    if (p < g.HW()) {
+        const size_t o = bi * g.NV() + p;
+        const float den = rho + 2.f * gam;
+        const float hb = Hbar[bi * g.HW() + p];
+        const float s = gam > 0.f ? A[o] + C[o] : 0.f;
+        const float h = (rho * Wn[o] + gam * s) / den;
+        Wn_bar[o] += rho / den * hb;
+        if (gam > 0.f) {
+            A_bar[o] += gam / den * hb;
+            C_bar[o] += gam / den * hb;
+            gb = (double)(hb * (s - 2.f * h) / den);
+        }
+        rb = (double)(hb * (Wn[o] - h) / den);
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        rb += __shfl_down_sync(0xffffffffu, rb, off);
+        gb += __shfl_down_sync(0xffffffffu, gb, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(acc + 0, rb);
+        atomicAdd(acc + 1, gb);
+    }
+}
+
+// ---- Huber-TV prox: dual projected gradient ----------------------------------
+// q at (i, j) from p (both components, [bi] planes) and h.
+__device__ __forceinline__ float qval(const float *p1, const float *p2, const float *h, int i,
+                                      int j, int H, int W, float inv_theta)
+{
+    return divp(p1, p2, i, j, H, W) - h[(size_t)i * W + j] * inv_theta;
+}
+
+struct DualArgs {
+    const float *P;  // [B][2][H][W] p^t
+    float *Pn;       // [B][2][H][W] p^{t+1}
+    const float *Hb; // [B][H][W]
+    Geo g;
+    float inv_theta, tau, kappa;
+};
+
+// a = p + tau (grad q - kappa p) at pixel (i, j) of item bi; returns a1, a2.
+__device__ __forceinline__ void dual_a(const float *p1, const float *p2, const float *h, int i,
+                                       int j, int H, int W, float inv_theta, float tau, float kappa,
+                                       float &a1, float &a2)
+{
+    const float qc = qval(p1, p2, h, i, j, H, W, inv_theta);
+    const float gx = i < H - 1 ? qval(p1, p2, h, i + 1, j, H, W, inv_theta) - qc : 0.f;
+    const float gy = j < W - 1 ? qval(p1, p2, h, i, j + 1, H, W, inv_theta) - qc : 0.f;
+    const size_t o = (size_t)i * W + j;
+    a1 = p1[o] + tau * (gx - kappa * p1[o]);
+    a2 = p2[o] + tau * (gy - kappa * p2[o]);
+}
+
+__global__ void dual_fwd_kernel(const DualArgs A)
+{
+    const size_t p = blockIdx.x * (size_t)kT + threadIdx.x;
+    const int bi = blockIdx.y;
+    const Geo &g = A.g;
+    if (p >= g.HW()) return;
+    const int i = (int)(p / g.W), j = (int)(p % g.W);
+    const float *p1 = A.P + (size_t)bi * 2 * g.HW(), *p2 = p1 + g.HW();
+    const float *h = A.Hb + (size_t)bi * g.HW();
+    float a1, a2;
+    dual_a(p1, p2, h, i, j, g.H, g.W, A.inv_theta, A.tau, A.kappa, a1, a2);
+    const float sc = 1.f / fmaxf(1.f, sqrtf(a1 * a1 + a2 * a2));
+    float *n1 = A.Pn + (size_t)bi * 2 * g.HW(), *n2 = n1 + g.HW();
+    n1[p] = a1 * sc;
+    n2[p] = a2 * sc;
+}
+
+// u_n = h - theta div p; d_n = w_n - u_n.
+__global__ void prox_out_kernel(const float *__restrict__ P, const float *__restrict__ Hb, Geo g,
+                                float theta, const float *__restrict__ Wn, float *__restrict__ Un,
+                                float *__restrict__ Dn)
+{
+    const size_t p = blockIdx.x * (size_t)kT + threadIdx.x;
+    const int bi = blockIdx.y;
+    if (p >= g.HW()) return;
+    const int i = (int)(p / g.W), j = (int)(p % g.W);
+    const float *p1 = P + (size_t)bi * 2 * g.HW(), *p2 = p1 + g.HW();
+    const float u = Hb[bi * g.HW() + p] - theta * divp(p1, p2, i, j, g.H, g.W);
+    const size_t o = bi * g.NV() + p;
+    Un[o] = u;
+    if (Dn) Dn[o] = Wn[o] - u;
+}
+
+// Reverse of prox_out: ubar -> hbar (set), pbar^T = theta grad ubar; theta
+// partial -<ubar, div p^T> into acc[2].
+__global__ void prox_out_bwd_kernel(const float *__restrict__ P, Geo g, float theta,
+                                    const float *__restrict__ Ubar_n, float *__restrict__ Hbar,
+                                    float *__restrict__ Pbar, double *__restrict__ acc)
+{
+    const size_t p = blockIdx.x * (size_t)kT + threadIdx.x;
+    const int bi = blockIdx.y;
+    double tb = 0.0;
+    if (p < g.HW()) {
+        const int i = (int)(p / g.W), j = (int)(p % g.W);
+        const float *p1 = P + (size_t)bi * 2 * g.HW(), *p2 = p1 + g.HW();
+        const float *ub = Ubar_n + (size_t)bi * g.NV();
+        const float uc = ub[p];
+        Hbar[bi * g.HW() + p] = uc;
+        tb = (double)(-uc * divp(p1, p2, i, j, g.H, g.W));
+        // d/dp of -theta <ubar, div p> = theta grad ubar (div = -grad^T)
+        float *b1 = Pbar + (size_t)bi * 2 * g.HW(), *b2 = b1 + g.HW();
+        b1[p] = i < g.H - 1 ? theta * (ub[p + g.W] - uc) : 0.f;
+        b2[p] = j < g.W - 1 ? theta * (ub[p + 1] - uc) : 0.f;
+    }
+    for (int off = 16; off > 0; off >>= 1) tb += __shfl_down_sync(0xffffffffu, tb, off);
+    if ((threadIdx.x & 31) == 0) atomicAdd(acc + 2, tb);
+}
+
+// Reverse of one dual step, part 1: abar = J_proj(a)^T pbar^{t+1}; the kappa
+// term's theta partial: dkappa = -tau <abar, p>, dtheta += dkappa * (-eps/theta^2).
+__global__ void dual_bwd_a_kernel(const DualArgs A, const float *__restrict__ Pbar_next,
+                                  float *__restrict__ Abar, float eps, double *__restrict__ acc)
+{
+    const size_t p = blockIdx.x * (size_t)kT + threadIdx.x;
+    const int bi = blockIdx.y;
+    const Geo &g = A.g;
+    double tb = 0.0;
+    if (p < g.HW()) {
+        const int i = (int)(p / g.W), j = (int)(p % g.W);
+        const float *p1 = A.P + (size_t)bi * 2 * g.HW(), *p2 = p1 + g.HW();
+        const float *h = A.Hb + (size_t)bi * g.HW();
+        float a1, a2;
+        dual_a(p1, p2, h, i, j, g.H, g.W, A.inv_theta, A.tau, A.kappa, a1, a2);
+        const float *n1 = Pbar_next + (size_t)bi * 2 * g.HW(), *n2 = n1 + g.HW();
+        const float b1 = n1[p], b2 = n2[p];
+        const float na = sqrtf(a1 * a1 + a2 * a2);
+        float o1 = b1, o2 = b2;
+        if (na > 1.f) {  // J = (I - a a^T / |a|^2) / |a|, symmetric
+            const float dot = (a1 * b1 + a2 * b2) / (na * na);
+            o1 = (b1 - a1 * dot) / na;
+            o2 = (b2 - a2 * dot) / na;
+        }
+        float *ab1 = Abar + (size_t)bi * 2 * g.HW(), *ab2 = ab1 + g.HW();
+        ab1[p] = o1;
+        ab2[p] = o2;
+        const float kbar = -A.tau * (o1 * p1[p] + o2 * p2[p]);
+        const float theta = 1.f / A.inv_theta;
+        tb = (double)(kbar * (-eps / (theta * theta)));
+    }
+    for (int off = 16; off > 0; off >>= 1) tb += __shfl_down_sync(0xffffffffu, tb, off);
+    if ((threadIdx.x & 31) == 0) atomicAdd(acc + 2, tb);
+}
+
+// qbar = tau * grad^T abar = -tau div abar (a depends on q through tau grad q).
+__device__ __forceinline__ float qbar_at(const float *ab1, const float *ab2, int i, int j, int H,
+                                         int W, float tau)
+{
+    return -tau * divp(ab1, ab2, i, j, H, W);
+}
+
+// Reverse of one dual step, part 2: pbar^t = (1 - tau kappa) abar - grad qbar;
+// hbar -= qbar / theta; theta partial <qbar, h> / theta^2.
+__global__ void dual_bwd_b_kernel(const DualArgs A, const float *__restrict__ Abar,
+                                  float *__restrict__ Pbar, float *__restrict__ Hbar,
+                                  double *__restrict__ acc)
+{
+    const size_t p = blockIdx.x * (size_t)kT + threadIdx.x;
+    const int bi = blockIdx.y;
+    const Geo &g = A.g;
+    double tb = 0.0;
+    if (p < g.HW()) {
+        const int i = (int)(p / g.W), j = (int)(p % g.W);
+        const float *ab1 = Abar + (size_t)bi * 2 * g.HW(), *ab2 = ab1 + g.HW();
+        const float qc = qbar_at(ab1, ab2, i, j, g.H, g.W, A.tau);
+        const float gx = i < g.H - 1 ? qbar_at(ab1, ab2, i + 1, j, g.H, g.W, A.tau) - qc : 0.f;
+        const float gy = j < g.W - 1 ? qbar_at(ab1, ab2, i, j + 1, g.H, g.W, A.tau) - qc : 0.f;
+        const float damp = 1.f - A.tau * A.kappa;
+        float *pb1 = Pbar + (size_t)bi * 2 * g.HW(), *pb2 = pb1 + g.HW();
+        // q = div p - h/theta: dq/dp = div, so pbar += div^T qbar = -grad qbar
+        pb1[p] = damp * ab1[p] - gx;
+        pb2[p] = damp * ab2[p] - gy;
+        const float hv = A.Hb[bi * g.HW() + p];
+        Hbar[bi * g.HW() + p] -= qc * A.inv_theta;
+        tb = (double)(qc * hv * A.inv_theta * A.inv_theta);
+    }
+    for (int off = 16; off > 0; off >>= 1) tb += __shfl_down_sync(0xffffffffu, tb, off);
+    if ((threadIdx.x & 31) == 0) atomicAdd(acc + 2, tb);
+}
+
+// lbar -> dL/dlogits already includes m (1 - m); Uold_bar etc. are plain adds.
+__global__ void axpy_kernel(float *__restrict__ y, const float *__restrict__ x, float a,
+                            size_t n)
+{
+    for (size_t i = blockIdx.x * (size_t)kT + threadIdx.x; i < n; i += (size_t)gridDim.x * kT)
+        y[i] += a * x[i];
+}
+
+// ---- host side ---------------------------------------------------------------
+struct Ws {
+    float *U, *D, *Wb, *Hb, *Pa, *Pb, *PH, *Useg, *Dseg;
+    float *Ubar_new, *Ubar_old, *Wbar, *Dbar, *Hbar, *Pbar_a, *Pbar_b, *Abar;
+    double *acc;  // [3]: rho (direct), gamma (direct), theta (total)
+};
+
+inline size_t al(size_t x) { return (x + 255) & ~size_t(255); }
+
+size_t ws_bytes(const Geo &g, int T, int S)
+{
+    const size_t nv = (size_t)g.B * g.NV() * 4, hw = (size_t)g.B * g.HW() * 4;
+    return al(nv) * 3 + al(hw) + 2 * al(2 * hw) + al((size_t)(T + 1) * 2 * hw) +
+           2 * al((size_t)(S + 1) * nv) + al(nv) * 4 + al(hw) + 3 * al(2 * hw) + al(64);
+}
+
+Ws carve(void *base, const Geo &g, int T, int S)
+{
+    const size_t nv = (size_t)g.B * g.NV() * 4, hw = (size_t)g.B * g.HW() * 4;
+    char *p = (char *)base;
+    auto take = [&](size_t n) {
+        char *r = p;
+        p += al(n);
+        return (float *)r;
+    };
+    Ws w;
+    w.U = take(nv);
+    w.D = take(nv);
+    w.Wb = take(nv);
+    w.Hb = take(hw);
+    w.Pa = take(2 * hw);
+    w.Pb = take(2 * hw);
+    w.PH = take((size_t)(T + 1) * 2 * hw);
+    w.Useg = take((size_t)(S + 1) * nv);
+    w.Dseg = take((size_t)(S + 1) * nv);
+    w.Ubar_new = take(nv);
+    w.Ubar_old = take(nv);
+    w.Wbar = take(nv);
+    w.Dbar = take(nv);
+    w.Hbar = take(hw);
+    w.Pbar_a = take(2 * hw);
+    w.Pbar_b = take(2 * hw);
+    w.Abar = take(2 * hw);
+    w.acc = (double *)take(64);
+    return w;
+}
+
+struct Prm {
+    float rho, lam, gam, tau, eps;
+    int K, T, S;
+    float theta() const { return lam / (rho + 2.f * gam); }
+};
+
+inline dim3 pgrid(const Geo &g) { return dim3((unsigned)((g.HW() + kT - 1) / kT), g.B); }
+
+#define LAUNCH(kid, ...)                    \
+    do {                                    \
+        LaunchScope ls_((kid), s);          \
+        __VA_ARGS__;                        \
+        CSLSM_LAUNCHED();                   \
+    } while (0)
+
+// Neighbour slices of slice n at its Gauss-Seidel update (newest values): the
+// previous slice is already new (old u_{Z-1} for n = 0), the next still old
+// (new u_0 for n = Z-1).
+inline void neighbours(const Geo &g, int n, float *Uold, float *Unew, float *&A, float *&C)
+{
+    const size_t HW = g.HW();
+    A = n >= 1 ? Unew + (size_t)(n - 1) * HW : Uold + (size_t)(g.Z - 1) * HW;
+    C = n < g.Z - 1 ? Uold + (size_t)(n + 1) * HW : Unew;
+}
+
+// Runs one slice's prox (recording the dual iterates into PH when given).
+cslsm_status slice_prox(const Geo &g, const Prm &P, const float *Hb, float *Pa, float *Pb,
+                        float *PH, float **pT, cudaStream_t s)
+{
+    const float theta = P.theta();
+    const size_t hw2 = (size_t)g.B * 2 * g.HW();
+    const int T = theta > 0.f ? P.T : 0;
+    float *cur = PH ? PH : Pa;
+    CSLSM_CUDA(cudaMemsetAsync(cur, 0, hw2 * sizeof(float), s));
+    for (int t = 0; t < T; ++t) {
+        float *nxt = PH ? PH + (size_t)(t + 1) * hw2 : (cur == Pa ? Pb : Pa);
+        DualArgs A{cur, nxt, Hb, g, 1.f / theta, P.tau, P.eps / theta};
+        LAUNCH(K_DIFF, dual_fwd_kernel<<<pgrid(g), kT, 0, s>>>(A));
+        cur = nxt;
+    }
+    *pT = cur;
+    return CSLSM_OK;
+}
+
+// One forward iteration on (U, D) in place; writes v when vout != null.
+cslsm_status fwd_iter(const Geo &g, const Prm &P, const float *logits, const float *b, Ws &w,
+                      float *vout, cudaStream_t s)
+{
+    const float gam = g.Z > 1 ? P.gam : 0.f;
+    LAUNCH(K_DIFF, ux_fwd_kernel<<<pgrid(g), kT, 0, s>>>(w.U, w.D, logits, b, g, P.rho, w.Wb, vout));
+    const float theta = P.lam / (P.rho + 2.f * gam);
+    Prm Q = P;
+    Q.gam = gam;
+    for (int n = 0; n < g.Z; ++n) {
+        float *A, *C;
+        neighbours(g, n, w.U, w.U, A, C);  // in place: the array holds the newest values
+        const size_t off = (size_t)n * g.HW();
+        LAUNCH(K_DIFF, hform_kernel<<<pgrid(g), kT, 0, s>>>(w.Wb + off, A, C, g, P.rho, gam, w.Hb));
+        float *pT = nullptr;
+        cslsm_status e = slice_prox(g, Q, w.Hb, w.Pa, w.Pb, nullptr, &pT, s);
+        if (e) return e;
+        LAUNCH(K_DIFF, prox_out_kernel<<<pgrid(g), kT, 0, s>>>(pT, w.Hb, g, theta, w.Wb + off,
+                                                                 w.U + off, w.D + off));
+    }
+    return CSLSM_OK;
+}
+
+}  // namespace
+
+size_t unrolled_workspace_bytes(int B, int Z, int H, int W, int T, int S)
+{
+    return ws_bytes(Geo{B, Z, H, W}, T, S);
+}
+
+cslsm_status unrolled_forward(int B, int Z, int H, int W, float rho, float lam, float gam,
+                              int K, int T, float tau, float eps, int S, const float *logits,
+                              const float *b, float *vout, float *ckpt, void *ws, cudaStream_t s)
+{
+    const Geo g{B, Z, H, W};
+    const Prm P{rho, lam, gam, tau, eps, K, T, S};
+    Ws w = carve(ws, g, T, S);
+    const size_t nv = (size_t)B * g.NV();
+    CSLSM_CUDA(cudaMemsetAsync(w.U, 0, nv * 4, s));
+    CSLSM_CUDA(cudaMemsetAsync(w.D, 0, nv * 4, s));
+    for (int k = 0; k < K; ++k) {
+        if (k % S == 0 && ckpt) {
+            float *c = ckpt + (size_t)(k / S) * 2 * nv;
+            CSLSM_CUDA(cudaMemcpyAsync(c, w.U, nv * 4, cudaMemcpyDeviceToDevice, s));
+            CSLSM_CUDA(cudaMemcpyAsync(c + nv, w.D, nv * 4, cudaMemcpyDeviceToDevice, s));
+        }
+        cslsm_status e = fwd_iter(g, P, logits, b, w, k == K - 1 ? vout : nullptr, s);
+        if (e) return e;
+    }
+    return CSLSM_OK;
+}
+
+cslsm_status unrolled_backward(int B, int Z, int H, int W, float rho, float lam, float gam,
+                               int K, int T, float tau, float eps, int S, const float *logits,
+                               const float *b, const float *ckpt, const float *vbar,
+                               float *logits_bar, double *scal_bar, void *ws, cudaStream_t s)
+{
+    const Geo g{B, Z, H, W};
+    Prm P{rho, lam, gam, tau, eps, K, T, S};
+    const float gz = Z > 1 ? gam : 0.f;
+    P.gam = gz;
+    Ws w = carve(ws, g, T, S);
+    const size_t nv = (size_t)B * g.NV(), HW = g.HW(), hw2 = (size_t)B * 2 * HW;
+    const float den = rho + 2.f * gz, theta = lam / den;
+    CSLSM_CUDA(cudaMemsetAsync(w.acc, 0, 3 * sizeof(double), s));
+    CSLSM_CUDA(cudaMemsetAsync(logits_bar, 0, nv * 4, s));
+    // adjoint of the state after the last iteration: only v^K is observed
+    CSLSM_CUDA(cudaMemsetAsync(w.Ubar_new, 0, nv * 4, s));
+    CSLSM_CUDA(cudaMemsetAsync(w.Dbar, 0, nv * 4, s));
+    const int nseg = (K + S - 1) / S;
+    for (int sg = nseg - 1; sg >= 0; --sg) {
+        const int k0 = sg * S, k1 = std::min(K, k0 + S);
+        // recompute the segment's states u^k, d^k for k = k0 .. k1
+        const float *c = ckpt + (size_t)sg * 2 * nv;
+        CSLSM_CUDA(cudaMemcpyAsync(w.U, c, nv * 4, cudaMemcpyDeviceToDevice, s));
+        CSLSM_CUDA(cudaMemcpyAsync(w.D, c + nv, nv * 4, cudaMemcpyDeviceToDevice, s));
+        for (int k = k0; k <= k1; ++k) {
+            const int slot = k - k0;
+            CSLSM_CUDA(cudaMemcpyAsync(w.Useg + (size_t)slot * nv, w.U, nv * 4,
+                                       cudaMemcpyDeviceToDevice, s));
+            CSLSM_CUDA(cudaMemcpyAsync(w.Dseg + (size_t)slot * nv, w.D, nv * 4,
+                                       cudaMemcpyDeviceToDevice, s));
+            if (k < k1) {
+                cslsm_status e = fwd_iter(g, P, logits, b, w, nullptr, s);
+                if (e) return e;
+            }
+        }
+        for (int k = k1 - 1; k >= k0; --k) {
+            const int slot = k - k0;
+            float *Uo = w.Useg + (size_t)slot * nv, *Do = w.Dseg + (size_t)slot * nv;
+            float *Un = w.Useg + (size_t)(slot + 1) * nv;
+            // w^{k+1} from (u^k, d^k)
+            LAUNCH(K_DIFF, ux_fwd_kernel<<<pgrid(g), kT, 0, s>>>(Uo, Do, logits, b, g, rho, w.Wb,
+                                                                   nullptr));
+            // d^{k+1} = w - u^{k+1}:  wbar = dbar, ubar_new -= dbar
+            CSLSM_CUDA(cudaMemcpyAsync(w.Wbar, w.Dbar, nv * 4, cudaMemcpyDeviceToDevice, s));
+            LAUNCH(K_DIFF, axpy_kernel<<<4096, kT, 0, s>>>(w.Ubar_new, w.Dbar, -1.f, nv));
+            CSLSM_CUDA(cudaMemsetAsync(w.Ubar_old, 0, nv * 4, s));
+            // reverse Gauss-Seidel sweep
+            for (int n = Z - 1; n >= 0; --n) {
+                float *A, *C;
+                neighbours(g, n, Uo, Un, A, C);
+                float *Ab, *Cb;
+                neighbours(g, n, w.Ubar_old, w.Ubar_new, Ab, Cb);
+                const size_t off = (size_t)n * HW;
+                LAUNCH(K_DIFF, hform_kernel<<<pgrid(g), kT, 0, s>>>(w.Wb + off, A, C, g, rho, gz,
+                                                                    w.Hb));
+                float *pT = nullptr;
+                cslsm_status e = slice_prox(g, P, w.Hb, w.Pa, w.Pb, w.PH, &pT, s);
+                if (e) return e;
+                LAUNCH(K_DIFF, prox_out_bwd_kernel<<<pgrid(g), kT, 0, s>>>(
+                                   pT, g, theta, w.Ubar_new + off, w.Hbar, w.Pbar_a, w.acc));
+                const int Tn = theta > 0.f ? T : 0;
+                float *pb_in = w.Pbar_a, *pb_out = w.Pbar_b;
+                for (int t = Tn - 1; t >= 0; --t) {
+                    DualArgs Ad{w.PH + (size_t)t * hw2, nullptr, w.Hb, g, 1.f / theta, tau,
+                                eps / theta};
+                    LAUNCH(K_DIFF, dual_bwd_a_kernel<<<pgrid(g), kT, 0, s>>>(Ad, pb_in, w.Abar, eps,
+                                                                             w.acc));
+                    LAUNCH(K_DIFF, dual_bwd_b_kernel<<<pgrid(g), kT, 0, s>>>(Ad, w.Abar, pb_out,
+                                                                             w.Hbar, w.acc));
+                    std::swap(pb_in, pb_out);
+                }
+                LAUNCH(K_DIFF, hform_bwd_kernel<<<pgrid(g), kT, 0, s>>>(
+                                   w.Hbar, w.Wb + off, A, C, g, rho, gz, w.Wbar + off, Ab, Cb,
+                                   w.acc));
+            }
+            // x-update reverse: u^k, d^k adjoints
+            LAUNCH(K_DIFF, ux_bwd_kernel<<<pgrid(g), kT, 0, s>>>(
+                               Uo, Do, logits, b, g, rho, k == K - 1 ? vbar : nullptr, w.Wbar,
+                               w.Ubar_old, w.Dbar, logits_bar, w.acc));
+            std::swap(w.Ubar_new, w.Ubar_old);  // adjoint of u^k becomes the next "new"
+        }
+    }
+    // scalars: rho_direct, gamma_direct, theta_total -> (rho, lambda, gamma)
+    double acc[3];
+    CSLSM_CUDA(cudaMemcpyAsync(acc, w.acc, sizeof(acc), cudaMemcpyDeviceToHost, s));
+    CSLSM_CUDA(cudaStreamSynchronize(s));
+    const double dd = (double)den;
+    double out[3];
+    out[1] = acc[2] / dd;                                   // dtheta/dlambda = 1/den
+    out[0] = acc[0] - acc[2] * lam / (dd * dd);             // dtheta/drho = -lambda/den^2
+    out[2] = (Z > 1 ? acc[1] - 2.0 * acc[2] * lam / (dd * dd) : 0.0);
+    CSLSM_CUDA(cudaMemcpyAsync(scal_bar, out, sizeof(out), cudaMemcpyHostToDevice, s));
+    CSLSM_CUDA(cudaStreamSynchronize(s));
+    return CSLSM_OK;
+}
+
+}  // namespace cslsm

@@ -19,8 +19,9 @@
 // Inside a step every warp walks a band of rows top to bottom, one row per
 // iteration; each lane owns two adjacent columns (float2 shared accesses).
 // q of the next row is computed once and carried in registers, the right
-// neighbour's q and the left neighbour's p come from warp shuffles, so a
-// pixel-step costs 1.5 shared loads and 1 store.  A warp spans 64 columns
+// neighbour's q comes from a warp shuffle and the left neighbour's p from the
+// float2 holding the two columns to the left (no lane-divergent load), so a
+// pixel-step costs 2 shared loads and 1 store.  A warp spans 64 columns
 // and owns 62 of them (column chunks overlap by two so that every chunk
 // starts on an even column; the last lane only supplies q and p to its
 // neighbours).  p is double-buffered in shared memory,

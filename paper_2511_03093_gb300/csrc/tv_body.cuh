@@ -135,8 +135,7 @@ __device__ __forceinline__ void tv_tile_body(const TvLaunch &a, int bx, int by, 
             {
                 const float2 p1u = *reinterpret_cast<const float2 *>(a1 - PW);
                 const float2 gc = *reinterpret_cast<const float2 *>(gg);
-                float p2l = __shfl_up_sync(0xffffffffu, p2c.y, 1);
-                if (lane == 0) p2l = a2[-1];
+                const float p2l = reinterpret_cast<const float2 *>(a2 - 2)->y;
                 qc.x = fmaf(-gc.x, inv_theta, (p1c.x - p1u.x) + (p2c.x - p2l));
                 qc.y = fmaf(-gc.y, inv_theta, (p1c.y - p1u.y) + (p2c.y - p2c.x));
             }
@@ -148,8 +147,7 @@ __device__ __forceinline__ void tv_tile_body(const TvLaunch &a, int bx, int by, 
                 const float2 p1n = *reinterpret_cast<const float2 *>(a1);
                 const float2 p2n = *reinterpret_cast<const float2 *>(a2);
                 const float2 gn = *reinterpret_cast<const float2 *>(gg);
-                float p2l = __shfl_up_sync(0xffffffffu, p2n.y, 1);
-                if (lane == 0) p2l = a2[-1];
+                const float p2l = reinterpret_cast<const float2 *>(a2 - 2)->y;
                 float2 qn;
                 qn.x = fmaf(-gn.x, inv_theta, (p1n.x - p1c.x) + (p2n.x - p2l));
                 qn.y = fmaf(-gn.y, inv_theta, (p1n.y - p1c.y) + (p2n.y - p2n.x));
