@@ -137,6 +137,32 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def rank_workload(rank: int):
+    """Each rank reconstructs its own independent measurement (replicas)."""
+    import dataclasses
+
+    import synth
+
+    w = synth.WORKLOADS[WORKLOAD]
+    return dataclasses.replace(w, seed=w.seed + 100 * rank) if rank else w
+
+
+def max_over_ranks(values, world: int, device=None):
+    """Element-wise max of per-rank timings (the slowest rank sets the job time)."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor(list(values), dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t]
+
+
+def job_throughput(units_per_rank: float, world: int, max_ms: float) -> float:
+    """Whole-job voxel-iterations per second: all ranks' units over the slowest time."""
+    return units_per_rank * world / (max_ms / 1e3)
+
+
 def cpu_baseline(data, iters: int) -> dict:
     import oracle
 
@@ -209,11 +235,7 @@ def run_ours(args) -> None:
         dist.init_process_group("nccl", device_id=dev)
     cs.lib()
 
-    w = synth.WORKLOADS[WORKLOAD]
-    if rank:
-        import dataclasses
-
-        w = dataclasses.replace(w, seed=w.seed + 100 * rank)
+    w = rank_workload(rank)
     data = synth.generate(w)
     prm = cs.Params(**PARAMS)
     vox = w.Z * w.H * w.W
@@ -285,13 +307,10 @@ def run_ours(args) -> None:
         e2e_ms.append(s_ev.elapsed_time(e_ev))
     e2e_total = sum(e2e_ms)
 
-    t = torch.tensor([total_ms, e2e_total], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms, e2e_total = float(t[0]), float(t[1])
-    units = vox * PARAMS["iters"] * args.steps * world
-    value = units / (total_ms / 1e3)
-    e2e_value = units / (e2e_total / 1e3)
+    total_ms, e2e_total = max_over_ranks([total_ms, e2e_total], world, dev)
+    units = vox * PARAMS["iters"] * args.steps
+    value = job_throughput(units, world, total_ms)
+    e2e_value = job_throughput(units, world, e2e_total)
 
     if rank == 0:
         sm_max = (clk or {}).get("sm_max_mhz") or 2070.0
@@ -325,13 +344,183 @@ def run_ours(args) -> None:
         dist.destroy_process_group()
 
 
+# ---- secondary workloads (the other configurations of the method) -------------
+# Not the default line: `python bench.py --workload NAME` prints one JSON line.
+
+def _timed(fn, steps, warmup, flush):
+    import torch
+
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    return ms
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def _gen(args):
+    import synth
+
+    return synth.generate(synth.Workload(*args[:4], **args[4]))
+
+
+def run_secondary(args) -> None:
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_2511_03093_gb300 as cs
+    import synth
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    name = args.workload
+    out = {"workload": name, "steps": args.steps, "warmup": args.warmup}
+    peaks = _peaks()
+    if name in ("tikhonov_1024x1024x32", "tv_1024x1024x32", "bm3d_1024x1024x32",
+                "tv_128x128x8"):
+        wk = synth.WORKLOADS["tv_128x128x8" if name == "tv_128x128x8" else "bm3d_1024x1024x32"]
+        data = synth.generate(wk)
+        den = name.split("_")[0]
+        iters = 50 if name == "tv_128x128x8" else 30
+        prm = cs.Params(rho=1.0, lam=0.0 if den == "bm3d" else 0.05, gamma=0.0, iters=iters,
+                        denoiser=den, tv_inner=20, bm3d_sigma=0.05)
+        plan = cs.Plan(wk.H, wk.W, 1, wk.Z, torch.from_numpy(data["masks"]).to(dev))
+        b = torch.from_numpy(data["b"]).to(dev)
+        v = torch.empty((wk.Z, wk.H, wk.W), dtype=torch.float32, device=dev)
+        cs.set_autotune(1)
+        dom = {"tikhonov": "tikhonov_iter", "tv": "tv_tile", "bm3d": "bm3d_match"}[den]
+        cs.timing_read(dom, reset=True)
+        steps = max(1, args.steps if den != "bm3d" else min(args.steps, 2))
+        warm = max(1, args.warmup if den != "bm3d" else 1)
+        ms_w = _timed(lambda: plan.solve(b, prm, v_out=v), warm, 0, flush)
+        cs.timing_read(dom, reset=True)
+        cs.timing_enable(1)
+        ms = _timed(lambda: plan.solve(b, prm, v_out=v), steps, 0, flush)
+        cs.timing_enable(0)
+        n_dom, ms_dom = cs.timing_read(dom, reset=True)
+        vox = wk.Z * wk.H * wk.W
+        out.update(metric=METRIC, unit=UNIT, value=vox * iters / (sum(ms) / steps / 1e3),
+                   ms_per_step=sum(ms) / steps, iterations=iters, dominant=dom,
+                   dominant_share=ms_dom / sum(ms), psnr_db=oracle.psnr(v.double().cpu().numpy(),
+                                                                        data["x"]))
+        if den == "tikhonov":
+            R = wk.Z
+            bytes_launch = vox * (16.0 + 8.0 / R)
+            avg = ms_dom / n_dom / 1e3
+            out["roofline"] = {"bound": "hbm", "kernel": dom, "achieved": bytes_launch / avg / 1e9,
+                               "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                               "frac": bytes_launch / avg / 1e9 / peaks["hbm_gbs"],
+                               "bytes_per_launch": bytes_launch, "avg_launch_us": avg * 1e6}
+        elif den == "tv":
+            avg = ms_dom / n_dom / 1e3
+            fl = tv_flops_per_launch(wk.H, wk.W, 20) * wk.Z
+            out["roofline"] = {"bound": "alu", "kernel": dom, "achieved": fl / avg / 1e12,
+                               "peak": alu_peak_tflops(2070.0), "unit": "TFLOP/s",
+                               "frac": fl / avg / 1e12 / alu_peak_tflops(2070.0),
+                               "avg_launch_us": avg * 1e6,
+                               "streaming_model_GBs": vox * 424.2 / (sum(ms) / steps / iters / 1e3) / 1e9}
+        plan.close()
+    elif name == "batched_64":
+        import multiprocessing as mp
+
+        rng = np.random.default_rng(4000)
+        sizes = [(int(rng.choice([8, 16, 32])), int(rng.choice([256, 512, 768, 1024])))
+                 for _ in range(64)]
+        specs = [(f"b{i}", Z, S, S, dict(drift=True, mask_p=0.3, peak=50.0, sigma_g=0.02,
+                                           seed=4000 + i, n_blobs=min(2000, synth.blob_count(Z, S, S))))
+                 for i, (Z, S) in enumerate(sizes)]
+        with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 4)) as pool:
+            datas = pool.map(_gen, specs)
+        base = dict(rho=1.0, lam=0.05, gamma=0.2, iters=60, denoiser="tv", tv_inner=20)
+        items, plans = [], []
+        for (Z, S), dd in zip(sizes, datas):
+            plan = cs.Plan(S, S, 1, Z, torch.from_numpy(dd["masks"]).to(dev))
+            items.append((plan, torch.from_numpy(dd["b"]).to(dev),
+                          torch.empty((Z, S, S), dtype=torch.float32, device=dev)))
+        vox = sum(Z * S * S for Z, S in sizes)
+        res = {}
+        cs.set_autotune(1)
+        for storage in ("bf16", "fp32"):
+            batch = cs.Batch(items, cs.Params(storage=storage, **base))
+            ms = _timed(lambda: (batch.run(), batch.wait()), max(1, args.steps // 2), 1, flush)
+            ps = [oracle.psnr(v.double().cpu().numpy(), dd["x"]) for (_, _, v), dd in zip(items, datas)]
+            res[storage] = (sum(ms) / len(ms), ps)
+            batch.close()
+        plain_prm = cs.Params(storage="fp32", **base)
+
+        def plain():
+            for plan, b, v in items:
+                plan.solve(b, plain_prm, v_out=v)
+
+        ms_plain = _timed(plain, 1, 1, flush)
+        ps_plain = [oracle.psnr(v.double().cpu().numpy(), dd["x"]) for (_, _, v), dd in zip(items, datas)]
+        out.update(metric=METRIC, unit=UNIT, items=64, voxels=vox, iterations=60,
+                   value=vox * 60 / (res["bf16"][0] / 1e3),
+                   batched_bf16_ms=res["bf16"][0], batched_fp32_ms=res["fp32"][0],
+                   plain_fp32_ms=sum(ms_plain),
+                   plain_fp32_value=vox * 60 / (sum(ms_plain) / 1e3),
+                   batched_fp32_value=vox * 60 / (res["fp32"][0] / 1e3),
+                   max_dpsnr_bf16_vs_plain=max(abs(a - b) for a, b in zip(res["bf16"][1], ps_plain)),
+                   max_dpsnr_fp32_vs_plain=max(abs(a - b) for a, b in zip(res["fp32"][1], ps_plain)))
+    elif name == "unrolled_b8":
+        B, Z, H, W = 8, 16, 512, 512
+        g = torch.Generator(device="cuda").manual_seed(11)
+        logits = torch.randn(B, Z, H, W, generator=g, device=dev)
+        x = torch.rand(B, Z, H, W, generator=g, device=dev)
+        b = (torch.sigmoid(logits) * x).sum(1)
+        sc = [torch.tensor(v, device=dev, requires_grad=True) for v in (1.0, 0.05, 0.2)]
+        lg = logits.clone().requires_grad_(True)
+        fw, bw = [], []
+        for it in range(max(2, args.steps)):
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record()
+            v = cs.unrolled_admm(lg, b, *sc, iters=30, tv_steps=20, ckpt_every=5)
+            loss = 0.5 * ((v - x) ** 2).mean()
+            e1.record()
+            loss.backward()
+            e2.record()
+            e2.synchronize()
+            if it:
+                fw.append(e0.elapsed_time(e1))
+                bw.append(e1.elapsed_time(e2))
+        vox = B * Z * H * W
+        out.update(metric="unrolled PnP-ADMM voxel-iterations/s (forward + backward)", unit=UNIT,
+                   value=vox * 30 / ((np.mean(fw) + np.mean(bw)) / 1e3), forward_ms=float(np.mean(fw)),
+                   backward_ms=float(np.mean(bw)), batch=B, volume=[Z, H, W], iterations=30)
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=None,
+                    help="secondary workload: tikhonov_1024x1024x32, tv_1024x1024x32, "
+                         "bm3d_1024x1024x32, tv_128x128x8, batched_64, unrolled_b8")
     args = ap.parse_args()
+    if args.workload:
+        run_secondary(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
