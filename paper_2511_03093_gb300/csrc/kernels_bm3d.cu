@@ -20,8 +20,10 @@
 //    (SSD << 12 | window index, which orders like the global linear index);
 //    the warp merges the 32 lists with __reduce_min_sync.  Bit-exact.
 //  - Filtering (FP32): one warp per group.  Lane (k, h) holds rows 4h..4h+3 of
-//    patch k; the row DCT is in registers, the column DCT takes the partner
-//    lane's rows by shuffle, the Haar transform is a butterfly across lanes.
+//    patch k; the row DCT runs in registers, then the lane pair swaps 4x4
+//    blocks (shuffles) so that each lane holds 4 whole columns for the column
+//    DCT, and the Haar transform is a butterfly across lanes; every DCT
+//    coefficient is a compile-time constant-bank operand.
 //    A CTA owns an 8x8 block of references: it stages g (and the basic
 //    estimate) of the block's footprint in shared memory and aggregates the
 //    block's estimates there with shared atomics before one global atomic
@@ -237,49 +239,72 @@ __device__ __forceinline__ void dct_rows(float (&x)[4][kPS], bool inverse)
     }
 }
 
-__device__ __forceinline__ void dct_cols(float (&x)[4][kPS], int h, bool inverse)
+// Layout change between the row layout x[r][c] (rows 4h+r, all 8 columns) and
+// the column layout y[q][c] (all 8 rows, columns 4h+c) of a lane pair (h = 0,
+// 1): each lane keeps its own 4x4 block and swaps the other with its partner.
+// Register indices stay compile-time constants (h only drives selects).
+__device__ __forceinline__ void rows_to_cols(const float (&x)[4][kPS], float (&y)[kPS][4], int h)
 {
-    float other[4][kPS];
 #pragma unroll
     for (int r = 0; r < 4; ++r)
 #pragma unroll
-        for (int c = 0; c < kPS; ++c) other[r][c] = __shfl_xor_sync(0xffffffffu, x[r][c], 1);
-    float y[4][kPS];
+        for (int c = 0; c < 4; ++c) {
+            const float own = h ? x[r][4 + c] : x[r][c];
+            const float give = h ? x[r][c] : x[r][4 + c];
+            const float got = __shfl_xor_sync(0xffffffffu, give, 1);
+            y[r][c] = h ? got : own;
+            y[4 + r][c] = h ? own : got;
+        }
+}
+
+__device__ __forceinline__ void cols_to_rows(const float (&y)[kPS][4], float (&x)[4][kPS], int h)
+{
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        const int a = 4 * h + r;  // output row
+    for (int r = 0; r < 4; ++r)
 #pragma unroll
-        for (int c = 0; c < kPS; ++c) {
+        for (int c = 0; c < 4; ++c) {
+            const float own = h ? y[4 + r][c] : y[r][c];
+            const float give = h ? y[r][c] : y[4 + r][c];
+            const float got = __shfl_xor_sync(0xffffffffu, give, 1);
+            x[r][c] = h ? got : own;
+            x[r][4 + c] = h ? own : got;
+        }
+}
+
+// Column DCT in the column layout: Y[a][c] = sum_q C[a][q] X[q][c] (inverse:
+// C^T).  Every coefficient index is a compile-time constant.
+__device__ __forceinline__ void dct_cols(float (&y)[kPS][4], bool inverse)
+{
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        float t[kPS];
+#pragma unroll
+        for (int a = 0; a < kPS; ++a) {
             float s = 0.f;
 #pragma unroll
-            for (int q = 0; q < kPS; ++q) {
-                // input row q lives in this lane (h == q / 4) or the partner
-                const float v = ((q >> 2) == h) ? x[q & 3][c] : other[q & 3][c];
-                s = fmaf(inverse ? c_dct[q * kPS + a] : c_dct[a * kPS + q], v, s);
-            }
-            y[r][c] = s;
+            for (int q = 0; q < kPS; ++q)
+                s = fmaf(inverse ? c_dct[q * kPS + a] : c_dct[a * kPS + q], y[q][c], s);
+            t[a] = s;
         }
+#pragma unroll
+        for (int a = 0; a < kPS; ++a) y[a][c] = t[a];
     }
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int c = 0; c < kPS; ++c) x[r][c] = y[r][c];
 }
 
 // Orthonormal Haar along the group (patch index k), as butterflies on pairs
 // (k, k + s) with k % 2s == 0: low <- (lo + hi)/sqrt2, high <- (lo - hi)/sqrt2.
 // The butterfly matrix is its own inverse; the inverse runs the levels in
 // reverse order.
-__device__ __forceinline__ void haar(float (&x)[4][kPS], int k, int L, bool inverse)
+__device__ __forceinline__ void haar(float (&x)[kPS][4], int k, int L, bool inverse)
 {
     const float r2 = 0.70710678118654752f;
     for (int lev = 0; (1 << lev) < L; ++lev) {
         const int s = inverse ? (L >> (lev + 1)) : (1 << lev);
         const bool lo = (k % (2 * s)) == 0, hi = (k % (2 * s)) == s;
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
+        for (int r = 0; r < kPS; ++r)
 #pragma unroll
-            for (int c = 0; c < kPS; ++c) {
+            for (int c = 0; c < 4; ++c) {
                 const float o = __shfl_xor_sync(0xffffffffu, x[r][c], 2 * s);
                 if (lo) x[r][c] = (x[r][c] + o) * r2;
                 else if (hi) x[r][c] = (o - x[r][c]) * r2;
@@ -348,29 +373,32 @@ __global__ void __launch_bounds__(kFilterWarps * 32) bm3d_filter_kernel(const Fi
                 if (kWiener) b[rw][c] = act ? s_b[l] : 0.f;
             }
         dct_rows(x, false);
-        dct_cols(x, h, false);
-        haar(x, k, L, false);
+        float y[kPS][4], yb[kPS][4];
+        rows_to_cols(x, y, h);
+        dct_cols(y, false);
+        haar(y, k, L, false);
         float wsum = 0.f;
         if (kWiener) {
             dct_rows(b, false);
-            dct_cols(b, h, false);
-            haar(b, k, L, false);
+            rows_to_cols(b, yb, h);
+            dct_cols(yb, false);
+            haar(yb, k, L, false);
 #pragma unroll
-            for (int rw = 0; rw < 4; ++rw)
+            for (int q = 0; q < kPS; ++q)
 #pragma unroll
-                for (int c = 0; c < kPS; ++c) {
-                    const float bb = b[rw][c] * b[rw][c];
+                for (int c = 0; c < 4; ++c) {
+                    const float bb = yb[q][c] * yb[q][c];
                     const float wt = act ? bb / (bb + s2) : 0.f;
-                    x[rw][c] *= wt;
+                    y[q][c] *= wt;
                     wsum = fmaf(wt, wt, wsum);
                 }
         } else {
 #pragma unroll
-            for (int rw = 0; rw < 4; ++rw)
+            for (int q = 0; q < kPS; ++q)
 #pragma unroll
-                for (int c = 0; c < kPS; ++c) {
-                    const bool keep = act && fabsf(x[rw][c]) > thr;
-                    x[rw][c] = keep ? x[rw][c] : 0.f;
+                for (int c = 0; c < 4; ++c) {
+                    const bool keep = act && fabsf(y[q][c]) > thr;
+                    y[q][c] = keep ? y[q][c] : 0.f;
                     wsum += keep ? 1.f : 0.f;
                 }
         }
@@ -378,8 +406,9 @@ __global__ void __launch_bounds__(kFilterWarps * 32) bm3d_filter_kernel(const Fi
         for (int o = 16; o > 0; o >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
         const float weight = kWiener ? (wsum > 0.f ? 1.f / (s2 * wsum) : 1.f / s2)
                                      : 1.f / (s2 * fmaxf(wsum, 1.f));
-        haar(x, k, L, true);
-        dct_cols(x, h, true);
+        haar(y, k, L, true);
+        dct_cols(y, true);
+        cols_to_rows(y, x, h);
         dct_rows(x, true);
         if (act) {
 #pragma unroll

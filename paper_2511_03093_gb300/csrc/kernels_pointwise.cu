@@ -143,8 +143,8 @@ xupdate_w_kernel(const S *__restrict__ u, const S *__restrict__ d,
 }
 
 // One fused ADMM iteration with the Tikhonov prior (psi = ||u||^2):
-// x-update as above, then along z in order n = 0..Z-1 (Gauss-Seidel, cyclic,
-// always the newest neighbour values)
+// x-update as above (with w = v + d = u + phi_r e, one rounding), then along z
+// in order n = 0..Z-1 (Gauss-Seidel, cyclic, always the newest neighbour values)
 //   u_n = (rho w_n + gam (u_{n-1} + u_{n+1})) / (2 lam + rho + 2 gam),
 // and d_n = w_n - u_n  (= d + v - u).  One thread owns a pixel column for all
 // shots, so the in-place sweep needs no synchronisation.
@@ -183,7 +183,7 @@ tikhonov_iter_kernel(S *__restrict__ u, S *__restrict__ d, const float *__restri
                     const int o = base + r * HW;
                     const float g = ur[r] - dr[r];
                     const float v = bit(word, r) ? g + e : g;
-                    const float w = v + dr[r];
+                    const float w = bit(word, r) ? ur[r] + e : ur[r];  // v + d
                     float un;
                     if (gam > 0.f) {
                         float next;
@@ -212,6 +212,73 @@ tikhonov_iter_kernel(S *__restrict__ u, S *__restrict__ d, const float *__restri
     if (partials) {
         block_sum2(sdv, sv);
         if (threadIdx.x == 0) partials[2 * blockIdx.x] = sdv, partials[2 * blockIdx.x + 1] = sv;
+    }
+}
+
+// The same fused Tikhonov iteration, two adjacent pixel columns per thread
+// (8-byte accesses for FP32).  The first pass over a shot's planes reads u and
+// d once from HBM, accumulates sum_r phi_r (u_r - d_r) and parks u_r in shared
+// memory; the second pass takes u_r (and the next plane's u for the z term)
+// from shared memory, so HBM sees exactly one read of u, d and one write of
+// u, d per voxel.  The arithmetic per pixel is that of tikhonov_iter_kernel.
+template <typename S>
+__global__ void __launch_bounds__(kThreads)
+tikhonov_iter_v2_kernel(S *__restrict__ u, S *__restrict__ d, const float *__restrict__ b,
+                        const uint32_t *__restrict__ words, int wstride, int HW, int R, int N,
+                        float rho, float lam, float gam, float *__restrict__ v_out)
+{
+    extern __shared__ float2 su[];  // [R][kThreads]
+    const int t = threadIdx.x;
+    const int p = 2 * (blockIdx.x * kThreads + t);
+    if (p >= HW) return;
+    const int Z = N * R;
+    const float den = 2.f * lam + rho + 2.f * gam;
+    float2 prev = gam > 0.f ? ld2<S>(u + (size_t)(Z - 1) * HW + p) : make_float2(0.f, 0.f);
+    float2 first_new = make_float2(0.f, 0.f);
+    for (int j = 0; j < N; ++j) {
+        const uint2 wd = *reinterpret_cast<const uint2 *>(words + (size_t)j * wstride + p);
+        const float2 bj = *reinterpret_cast<const float2 *>(b + (size_t)j * HW + p);
+        const size_t base = (size_t)j * R * HW + p;
+        float2 s = make_float2(0.f, 0.f);
+#pragma unroll 8
+        for (int r = 0; r < R; ++r) {
+            const float2 uu = ld2<S>(u + base + (size_t)r * HW);
+            const float2 dd = ld2<S>(d + base + (size_t)r * HW);
+            su[r * kThreads + t] = uu;
+            if ((wd.x >> r) & 1u) s.x += uu.x - dd.x;
+            if ((wd.y >> r) & 1u) s.y += uu.y - dd.y;
+        }
+        const float ex = (bj.x - s.x) / (rho + (float)__popc(wd.x));
+        const float ey = (bj.y - s.y) / (rho + (float)__popc(wd.y));
+#pragma unroll 4
+        for (int r = 0; r < R; ++r) {
+            const int n = j * R + r;
+            const size_t o = base + (size_t)r * HW;
+            const float2 uu = su[r * kThreads + t];
+            const bool bx = (wd.x >> r) & 1u, by = (wd.y >> r) & 1u;
+            const float2 w = make_float2(bx ? uu.x + ex : uu.x, by ? uu.y + ey : uu.y);
+            float2 un;
+            if (gam > 0.f) {
+                float2 nx;
+                if (n == Z - 1) nx = first_new;
+                else if (r + 1 < R) nx = su[(r + 1) * kThreads + t];
+                else nx = ld2<S>(u + o + HW);  // next shot's first plane, still old
+                un.x = rnd<S>((rho * w.x + gam * (prev.x + nx.x)) / den);
+                un.y = rnd<S>((rho * w.y + gam * (prev.y + nx.y)) / den);
+                prev = un;
+                if (n == 0) first_new = un;
+            } else {
+                un = make_float2(rho * w.x / den, rho * w.y / den);
+            }
+            if (v_out) {  // v = (u - d) + phi e, with d before this iteration's store
+                const float2 dd = ld2<S>(d + o);
+                const float gx = uu.x - dd.x, gy = uu.y - dd.y;
+                *reinterpret_cast<float2 *>(v_out + o) = make_float2(bx ? gx + ex : gx,
+                                                                     by ? gy + ey : gy);
+            }
+            st2<S>(u + o, un);
+            st2<S>(d + o, make_float2(w.x - un.x, w.y - un.y));
+        }
     }
 }
 
@@ -350,6 +417,21 @@ cslsm_status tikhonov_typed(const Geom &g, Masks m, void *u_, void *d_, const fl
                             double *partials, cudaStream_t s)
 {
     S *u = (S *)u_, *d = (S *)d_;
+    const uintptr_t al = (uintptr_t)u | (uintptr_t)d | (uintptr_t)b | (uintptr_t)m.words |
+                         (uintptr_t)v_out;
+    if (!vprev && !partials && g.HW() % 2 == 0 && (al & 7) == 0) {
+        const int pairs = g.HW() / 2;
+        const size_t sm = sizeof(float2) * kThreads * (size_t)g.R;
+        static_assert(sizeof(float2) * kThreads * CSLSM_MAX_R <= 227 * 1024, "staging too large");
+        CSLSM_CUDA(cudaFuncSetAttribute(tikhonov_iter_v2_kernel<S>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)(sizeof(float2) * kThreads * CSLSM_MAX_R)));
+        LaunchScope ls(K_TIK_ITER, s);
+        tikhonov_iter_v2_kernel<S><<<(pairs + kThreads - 1) / kThreads, kThreads, sm, s>>>(
+            u, d, b, m.words, m.wstride, g.HW(), g.R, g.N, rho, lam, gam, v_out);
+        CSLSM_LAUNCHED();
+        return CSLSM_OK;
+    }
     const dim3 grid = pixel_grid(g.HW(), 1);
 #define TK(RM)                                                                            \
     tikhonov_iter_kernel<RM, S><<<grid, kThreads, 0, s>>>(u, d, b, m.words, m.wstride,   \

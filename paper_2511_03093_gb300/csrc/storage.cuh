@@ -65,6 +65,95 @@ __device__ __forceinline__ void st<__half>(__half *p, float v)
     *p = __float2half_rn(v);
 }
 
+// Two consecutive elements (8-byte aligned for float, 4-byte for 16-bit types).
+template <typename S>
+__device__ __forceinline__ float2 ld2(const S *p);
+template <>
+__device__ __forceinline__ float2 ld2<float>(const float *p)
+{
+    return *reinterpret_cast<const float2 *>(p);
+}
+template <>
+__device__ __forceinline__ float2 ld2<__nv_bfloat16>(const __nv_bfloat16 *p)
+{
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p));
+}
+template <>
+__device__ __forceinline__ float2 ld2<__half>(const __half *p)
+{
+    return __half22float2(*reinterpret_cast<const __half2 *>(p));
+}
+template <typename S>
+__device__ __forceinline__ void st2(S *p, float2 v);
+template <>
+__device__ __forceinline__ void st2<float>(float *p, float2 v)
+{
+    *reinterpret_cast<float2 *>(p) = v;
+}
+template <>
+__device__ __forceinline__ void st2<__nv_bfloat16>(__nv_bfloat16 *p, float2 v)
+{
+    *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(v.x, v.y);
+}
+template <>
+__device__ __forceinline__ void st2<__half>(__half *p, float2 v)
+{
+    *reinterpret_cast<__half2 *>(p) = __floats2half2_rn(v.x, v.y);
+}
+
+// Four consecutive elements (16-byte aligned for float, 8-byte for 16-bit types).
+template <typename S>
+__device__ __forceinline__ float4 ld4(const S *p);
+template <>
+__device__ __forceinline__ float4 ld4<float>(const float *p)
+{
+    return *reinterpret_cast<const float4 *>(p);
+}
+template <>
+__device__ __forceinline__ float4 ld4<__nv_bfloat16>(const __nv_bfloat16 *p)
+{
+    const uint2 r = *reinterpret_cast<const uint2 *>(p);
+    const __nv_bfloat162 a = *reinterpret_cast<const __nv_bfloat162 *>(&r.x);
+    const __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162 *>(&r.y);
+    const float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
+    return make_float4(fa.x, fa.y, fb.x, fb.y);
+}
+template <>
+__device__ __forceinline__ float4 ld4<__half>(const __half *p)
+{
+    const uint2 r = *reinterpret_cast<const uint2 *>(p);
+    const __half2 a = *reinterpret_cast<const __half2 *>(&r.x);
+    const __half2 b = *reinterpret_cast<const __half2 *>(&r.y);
+    const float2 fa = __half22float2(a), fb = __half22float2(b);
+    return make_float4(fa.x, fa.y, fb.x, fb.y);
+}
+
+template <typename S>
+__device__ __forceinline__ void st4(S *p, float4 v);
+template <>
+__device__ __forceinline__ void st4<float>(float *p, float4 v)
+{
+    *reinterpret_cast<float4 *>(p) = v;
+}
+template <>
+__device__ __forceinline__ void st4<__nv_bfloat16>(__nv_bfloat16 *p, float4 v)
+{
+    const __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
+    uint2 r;
+    r.x = *reinterpret_cast<const unsigned *>(&a);
+    r.y = *reinterpret_cast<const unsigned *>(&b);
+    *reinterpret_cast<uint2 *>(p) = r;
+}
+template <>
+__device__ __forceinline__ void st4<__half>(__half *p, float4 v)
+{
+    const __half2 a = __floats2half2_rn(v.x, v.y), b = __floats2half2_rn(v.z, v.w);
+    uint2 r;
+    r.x = *reinterpret_cast<const unsigned *>(&a);
+    r.y = *reinterpret_cast<const unsigned *>(&b);
+    *reinterpret_cast<uint2 *>(p) = r;
+}
+
 // The value a store of v into S followed by a load gives back.
 template <typename S>
 __device__ __forceinline__ float rnd(float v)
