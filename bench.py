@@ -71,8 +71,10 @@ def alu_peak_tflops(sm_mhz: float) -> float:
 
 
 def _kernel_hash() -> str:
-    p = os.path.join(ROOT, "paper_2511_03093_gb300", "csrc", "kernels_tv.cu")
-    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for f in ("kernels_tv.cu", "tv_body.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2511_03093_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def _traffic():
@@ -83,7 +85,7 @@ def _traffic():
         rec = json.load(open(p))
     except (OSError, ValueError):
         return None
-    if rec.get("kernels_tv_sha256_16") != _kernel_hash():
+    if rec.get("tv_sources_sha256_16") != _kernel_hash():
         return None
     return rec.get("dram_bytes_per_launch")
 
