@@ -323,7 +323,7 @@ struct FilterArgs {
 };
 
 template <bool kWiener>
-__global__ void __launch_bounds__(kFilterWarps * 32) bm3d_filter_kernel(const FilterArgs a)
+__global__ void __launch_bounds__(kFilterWarps * 32, 2) bm3d_filter_kernel(const FilterArgs a)
 {
     __shared__ double s_num[kFoot * kFootPitch], s_den[kFoot * kFootPitch];
     __shared__ float s_n[kFoot * kFootPitch];
@@ -363,35 +363,43 @@ __global__ void __launch_bounds__(kFilterWarps * 32) bm3d_filter_kernel(const Fi
         const bool act = k < L;
         const int lin = act ? a.lists[gi * kMaxGroup + k] : a.lists[gi * kMaxGroup];
         const int py = lin / W - f0, px = lin % W - g0;
-        float x[4][kPS], b[4][kPS];
-#pragma unroll
-        for (int rw = 0; rw < 4; ++rw)
-#pragma unroll
-            for (int c = 0; c < kPS; ++c) {
-                const int l = (py + 4 * h + rw) * kFootPitch + px + c;
-                x[rw][c] = act ? s_n[l] : 0.f;
-                if (kWiener) b[rw][c] = act ? s_b[l] : 0.f;
-            }
-        dct_rows(x, false);
-        float y[kPS][4], yb[kPS][4];
-        rows_to_cols(x, y, h);
-        dct_cols(y, false);
-        haar(y, k, L, false);
+        // Wiener: the shrinkage factors come from the guide's spectrum, taken
+        // first so that only the factors (not the guide's coefficients) stay live.
+        float x[4][kPS], y[kPS][4], wt[kPS][4];
         float wsum = 0.f;
         if (kWiener) {
-            dct_rows(b, false);
-            rows_to_cols(b, yb, h);
-            dct_cols(yb, false);
-            haar(yb, k, L, false);
+#pragma unroll
+            for (int rw = 0; rw < 4; ++rw)
+#pragma unroll
+                for (int c = 0; c < kPS; ++c)
+                    x[rw][c] = act ? s_b[(py + 4 * h + rw) * kFootPitch + px + c] : 0.f;
+            dct_rows(x, false);
+            rows_to_cols(x, y, h);
+            dct_cols(y, false);
+            haar(y, k, L, false);
 #pragma unroll
             for (int q = 0; q < kPS; ++q)
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
-                    const float bb = yb[q][c] * yb[q][c];
-                    const float wt = act ? bb / (bb + s2) : 0.f;
-                    y[q][c] *= wt;
-                    wsum = fmaf(wt, wt, wsum);
+                    const float bb = y[q][c] * y[q][c];
+                    wt[q][c] = act ? bb / (bb + s2) : 0.f;
+                    wsum = fmaf(wt[q][c], wt[q][c], wsum);
                 }
+        }
+#pragma unroll
+        for (int rw = 0; rw < 4; ++rw)
+#pragma unroll
+            for (int c = 0; c < kPS; ++c)
+                x[rw][c] = act ? s_n[(py + 4 * h + rw) * kFootPitch + px + c] : 0.f;
+        dct_rows(x, false);
+        rows_to_cols(x, y, h);
+        dct_cols(y, false);
+        haar(y, k, L, false);
+        if (kWiener) {
+#pragma unroll
+            for (int q = 0; q < kPS; ++q)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) y[q][c] *= wt[q][c];
         } else {
 #pragma unroll
             for (int q = 0; q < kPS; ++q)
