@@ -34,8 +34,9 @@ PARAMS = dict(rho=1.0, lam=0.05, gamma=0.2, iters=100, denoiser="tv", tv_inner=2
 METRIC = "PnP-ADMM voxel-iterations/s"
 UNIT = "voxel-it/s"
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
-DOMINANT = "tv_tile"
-TIMING_PERIOD = 16  # sample every 16th launch of each kernel with CUDA events
+DOMINANT = "tvz_sweep"  # one launch = the TV u-step of all 16 slices (z Gauss-Seidel sweep)
+DOMINANT_SOURCES = ("kernels_tvz.cu", "tv_body.cuh")
+TIMING_PERIOD = 4  # sample every 4th launch of each kernel with CUDA events
 
 
 def _env_int(k, d):
@@ -70,9 +71,9 @@ def alu_peak_tflops(sm_mhz: float) -> float:
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
-def _kernel_hash() -> str:
+def _kernel_hash(sources=DOMINANT_SOURCES) -> str:
     h = hashlib.sha256()
-    for f in ("kernels_tv.cu", "tv_body.cuh"):
+    for f in sources:
         h.update(open(os.path.join(ROOT, "paper_2511_03093_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -80,12 +81,12 @@ def _kernel_hash() -> str:
 def _traffic():
     """DRAM bytes per launch of the dominant kernel from the committed ncu summary,
     if it was taken on the kernel source as it is now."""
-    p = os.path.join(ROOT, "profiles", "tv_tile_tvz_512x512x16.json")
+    p = os.path.join(ROOT, "profiles", f"{DOMINANT}_{WORKLOAD}.json")
     try:
         rec = json.load(open(p))
     except (OSError, ValueError):
         return None
-    if rec.get("tv_sources_sha256_16") != _kernel_hash():
+    if rec.get("sources_sha256_16") != _kernel_hash():
         return None
     return rec.get("dram_bytes_per_launch")
 
@@ -319,7 +320,7 @@ def run_ours(args) -> None:
         roof = None
         if n_dom:
             avg_s = ms_dom / n_dom / 1e3
-            achieved = tv_flops_per_launch(w.H, w.W, PARAMS["tv_inner"]) / avg_s / 1e12
+            achieved = w.Z * tv_flops_per_launch(w.H, w.W, PARAMS["tv_inner"]) / avg_s / 1e12
             peak = alu_peak_tflops(sm_max)
             roof = {"bound": "alu", "kernel": DOMINANT, "achieved": achieved, "peak": peak,
                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": _traffic(),
@@ -337,7 +338,7 @@ def run_ours(args) -> None:
                     "h2d_bytes_per_step": int(masks_h.numel() + b_h.numel() * 4),
                     "d2h_bytes_per_step": int(v_h.numel() * 4)},
             "gpu_launches": int(launches), "clocks": clk,
-            "tv_shape": cs.tv_shape(w.H, w.W, PARAMS["tv_inner"], 1),
+            "zsweep_shape": cs.zsweep_shape(w.H, w.W, w.Z, PARAMS["tv_inner"]),
             "step_ms": [round(x, 3) for x in step_ms],
         }
         print(json.dumps(out), flush=True)

@@ -36,7 +36,7 @@ extern "C" {
 #endif
 
 #define CSLSM_MAX_R 32
-#define CSLSM_ABI_VERSION 2
+#define CSLSM_ABI_VERSION 3
 
 typedef enum {
     CSLSM_OK = 0,
@@ -327,6 +327,33 @@ cslsm_status cslsm_set_autotune(int mode);
  * region rows}.  steps <= 24 (longer proxes run in chunks). */
 cslsm_status cslsm_tv_shape(int H, int W, int steps, int nslices, int *shape4);
 
+/* Persistent z sweep (process-wide setting).  With gamma > 0 the TV u-step
+ * of cslsm_admm_solve (the Gauss-Seidel sweep over slices of Sec. III-C) runs
+ * in ONE cooperative launch per ADMM iteration (enable = 1, the default):
+ * every CTA owns one tile of every slice and trades the dual field of its
+ * tile with its neighbours every few Chambolle steps.  enable = 0 runs one
+ * tile-kernel launch per slice instead; the two give bit-identical results.
+ * tiling < 0: the tiling is chosen per (device, H, W, Z, steps, storage) key
+ * by a cost model, or under cslsm_set_autotune(1) by timing every tiling once
+ * on scratch copies of u and d (outside stream capture; synchronises the
+ * stream).  0 <= tiling < cslsm_zsweep_num_tilings(): force that tiling
+ * (tests).  wait_limit_s (> 0, default 2) bounds every device-side wait of the
+ * sweep; when one gives up, every CTA stops and the solve returns
+ * CSLSM_ERR_TIMEOUT.  test_stall != 0 makes one CTA wait for an epoch that is
+ * never published (tests of the timeout path only).  A solve that used the
+ * sweep reads the error word at its end (synchronising `stream` unless it is
+ * being captured). */
+cslsm_status cslsm_zsweep_config(int enable, int tiling, double wait_limit_s, int test_stall);
+
+/* Number of sweep tilings (steps per phase x target CTAs per SM x row shape:
+ * warps per CTA and rows per warp). */
+int cslsm_zsweep_num_tilings(void);
+
+/* The tiling a sweep of this geometry would use now (on the current device):
+ * out8 (host int[8]) = {tiling, steps per phase, rows per warp, warps per CTA,
+ * tile rows, tile columns, region rows, tiles}. */
+cslsm_status cslsm_zsweep_shape(int H, int W, int Z, int steps, int storage, int *out8);
+
 /* ---- instrumentation (benchmarks, tracing) ------------------------------ */
 
 /* Number of kernels the library has launched in this process so far. */
@@ -337,7 +364,8 @@ unsigned long long cslsm_launch_count(void);
  * events add a little GPU time of their own); 0 switches sampling off.
  * Kernel names: "pack_masks", "forward", "adjoint", "xupdate_w",
  * "tikhonov_iter", "tikhonov_prox", "tv_tile", "psnr_partials",
- * "reduce_finish". */
+ * "reduce_finish", "bm3d_prep", "bm3d_match", "bm3d_filter", "bm3d_finish",
+ * "batch_persistent", "unrolled", "tvz_sweep". */
 cslsm_status cslsm_timing_enable(int period);
 
 /* Waits for the recorded events of `kernel` and returns how many launches

@@ -152,6 +152,12 @@ def lib() -> ctypes.CDLL:
     L.cslsm_tv_shape.restype = I
     L.cslsm_set_autotune.argtypes = [I]
     L.cslsm_set_autotune.restype = I
+    L.cslsm_zsweep_config.argtypes = [I, I, ctypes.c_double, I]
+    L.cslsm_zsweep_config.restype = I
+    L.cslsm_zsweep_num_tilings.argtypes = []
+    L.cslsm_zsweep_num_tilings.restype = I
+    L.cslsm_zsweep_shape.argtypes = [I, I, I, I, I, P]
+    L.cslsm_zsweep_shape.restype = I
     L.cslsm_bm3d_num_refs.argtypes = [I, I]
     L.cslsm_bm3d_num_refs.restype = I
     L.cslsm_launch_count.argtypes = []
@@ -352,6 +358,28 @@ def tv_shape(H: int, W: int, steps: int, nslices: int) -> dict:
     _check(lib().cslsm_tv_shape(int(H), int(W), int(steps), int(nslices), buf),
            "cslsm_tv_shape")
     return {"variant": buf[0], "tile_rows": buf[1], "tile_cols": buf[2], "region_rows": buf[3]}
+
+
+def zsweep_config(enable: bool = True, tiling: int = -1, wait_limit_s: float = 2.0,
+                  test_stall: bool = False) -> None:
+    """Persistent z sweep of the TV u-step (gamma > 0): on/off, forced tiling
+    (-1: chosen per geometry), device-side wait limit, timeout test hook."""
+    _check(lib().cslsm_zsweep_config(int(bool(enable)), int(tiling), float(wait_limit_s),
+                                     int(bool(test_stall))), "cslsm_zsweep_config")
+
+
+def zsweep_num_tilings() -> int:
+    return int(lib().cslsm_zsweep_num_tilings())
+
+
+def zsweep_shape(H: int, W: int, Z: int, steps: int, storage: str = "fp32") -> dict:
+    """The sweep tiling a solve of this geometry uses now."""
+    buf = (ctypes.c_int * 8)()
+    _check(lib().cslsm_zsweep_shape(int(H), int(W), int(Z), int(steps), STORAGE[storage], buf),
+           "cslsm_zsweep_shape")
+    keys = ("tiling", "steps_per_phase", "rows_per_warp", "warps", "tile_rows", "tile_cols",
+            "region_rows", "tiles")
+    return dict(zip(keys, list(buf)))
 
 
 def denoise_bm3d_noalloc(x: torch.Tensor, sigma: float, out: torch.Tensor | None = None,

@@ -47,6 +47,7 @@ struct cslsm_plan_s {
     double *red_out = nullptr;  // 2 doubles
     void *bm3d_ws = nullptr;     // BM3D workspace (zero-filled on allocation)
     size_t bm3d_ws_bytes = 0;
+    ZsweepWs zs;                 // persistent z sweep (TV, gamma > 0)
 };
 
 namespace {
@@ -117,6 +118,7 @@ void free_plan(cslsm_plan_s *p)
     cudaFree(p->w);
     cudaFree(p->vprev);
     cudaFree(p->pbuf);
+    zsweep_release(p->zs);
     cudaFree(p->partials);
     cudaFree(p->red_out);
     cudaFree(p->bm3d_ws);
@@ -306,6 +308,7 @@ cslsm_status cslsm_admm_solve(cslsm_plan plan, const float *b, const cslsm_admm_
     int k = 0;
     double rel = -1.0;
     bool stopped = false;
+    bool used_zsweep = false;
     for (k = 0; k < prm->iters; ++k) {
         const bool last = (k == prm->iters - 1);
         const bool check = use_tol && k > 0 && ((k + 1) % prm->check_every == 0 || last);
@@ -368,11 +371,27 @@ cslsm_status cslsm_admm_solve(cslsm_plan plan, const float *b, const cslsm_admm_
                 st = tv_prox_slices(a, plan->pbuf, s);
                 if (st) return st;
             } else {
-                a.nslices = 1;
-                for (int n = 0; n < g.Z(); ++n) {
-                    a.n0 = n;
-                    st = tv_prox_slices(a, plan->pbuf, s);
-                    if (st) return st;
+                a.n0 = 0;
+                a.nslices = g.Z();
+                bool swept = false;
+                if (zsweep_applies(a)) {
+                    if (!plan->zs.pbuf) {
+                        CSLSM_CUDA(cudaStreamSynchronize(s));
+                        st = zsweep_reserve(plan->zs, g.H, g.W);
+                        if (st) return st;
+                    }
+                    st = zsweep_run(a, plan->zs, s);
+                    if (st && !(st == CSLSM_ERR_UNSUPPORTED && !zsweep_forced())) return st;
+                    swept = st == CSLSM_OK;  // else: no tiling fits; per-slice launches
+                    used_zsweep = used_zsweep || swept;
+                }
+                if (!swept) {
+                    a.nslices = 1;
+                    for (int n = 0; n < g.Z(); ++n) {
+                        a.n0 = n;
+                        st = tv_prox_slices(a, plan->pbuf, s);
+                        if (st) return st;
+                    }
                 }
             }
         }
@@ -391,6 +410,10 @@ cslsm_status cslsm_admm_solve(cslsm_plan plan, const float *b, const cslsm_admm_
                 break;
             }
         }
+    }
+    if (used_zsweep) {
+        st = zsweep_check(plan->zs, s);
+        if (st) return st;
     }
     if (stopped)  // v^{k} of the final iteration is in vprev
         CSLSM_CUDA(cudaMemcpyAsync(v_out, plan->vprev, sizeof(float) * nv,
@@ -748,6 +771,26 @@ cslsm_status cslsm_tv_shape(int H, int W, int steps, int nslices, int *shape4)
     CHECK_ARG(steps >= 0 && steps <= tv_max_steps_per_launch(), "steps must be in [0, %d]",
               tv_max_steps_per_launch());
     return tv_query_shape(H, W, steps, nslices, shape4);
+}
+
+cslsm_status cslsm_zsweep_config(int enable, int tiling, double wait_limit_s, int test_stall)
+{
+    CHECK_ARG(enable == 0 || enable == 1, "enable must be 0 or 1");
+    CHECK_ARG(tiling < zsweep_num_candidates(), "tiling must be < %d", zsweep_num_candidates());
+    CHECK_ARG(std::isfinite(wait_limit_s) && wait_limit_s > 0.0 && wait_limit_s <= 3600.0,
+              "wait_limit_s must be in (0, 3600]");
+    zsweep_config(enable, tiling < 0 ? -1 : tiling, wait_limit_s, test_stall != 0);
+    return CSLSM_OK;
+}
+
+int cslsm_zsweep_num_tilings(void) { return zsweep_num_candidates(); }
+
+cslsm_status cslsm_zsweep_shape(int H, int W, int Z, int steps, int storage, int *out8)
+{
+    CHECK_ARG(out8 != nullptr, "out8 is NULL");
+    CHECK_ARG(H >= 1 && W >= 1 && Z >= 2 && steps >= 1, "need H, W >= 1, Z >= 2, steps >= 1");
+    CHECK_ARG(storage >= CSLSM_STORE_FP32 && storage <= CSLSM_STORE_FP16, "bad storage");
+    return zsweep_query(H, W, Z, steps, storage, out8);
 }
 
 int cslsm_bm3d_num_refs(int H, int W) { return (H >= 1 && W >= 1) ? bm3d_nref(H, W) : 0; }

@@ -30,7 +30,8 @@ void set_error(const char *fmt, ...);
 // Kernels of the library, for launch accounting and sampled timing (timing.cu).
 enum KernelId {
     K_PACK = 0, K_FORWARD, K_ADJOINT, K_XUPDATE, K_TIK_ITER, K_TIK_PROX, K_TV_TILE, K_PSNR,
-    K_REDUCE, K_BM3D_PREP, K_BM3D_MATCH, K_BM3D_FILTER, K_BM3D_FINISH, K_BATCH, K_DIFF, K_COUNT
+    K_REDUCE, K_BM3D_PREP, K_BM3D_MATCH, K_BM3D_FILTER, K_BM3D_FINISH, K_BATCH, K_DIFF, K_TVZ,
+    K_COUNT
 };
 
 // Wrap every kernel launch: counts it and, when timing is on, records CUDA
@@ -121,6 +122,31 @@ void tv_set_mode(int mode);
 int tv_get_mode();
 // The shape (variant, TH, TW, RH) a launch of this geometry would use now.
 cslsm_status tv_query_shape(int H, int W, int T, int nslices, int *out4);
+
+// ---- persistent z sweep of the TV u-step (kernels_tvz.cu) -----------------
+// Workspace of a plan: the dual field handed between phases ([2][2][H][W]
+// floats), per-tile epoch flags, the error word, and the next epoch base.
+struct ZsweepWs {
+    float *pbuf = nullptr;
+    size_t pbuf_floats = 0;
+    unsigned *flags = nullptr;
+    int *err = nullptr;
+    int max_tiles = 0;
+    unsigned next_base = 0;
+};
+// True when the sweep handles this u-step: TV with gamma > 0 over all slices
+// and the sweep enabled.
+bool zsweep_applies(const TvSlices &a);
+cslsm_status zsweep_reserve(ZsweepWs &ws, int H, int W);
+void zsweep_release(ZsweepWs &ws);
+// The whole Gauss-Seidel sweep n = 0 .. Z-1 in one cooperative launch.
+cslsm_status zsweep_run(const TvSlices &a, ZsweepWs &ws, cudaStream_t s);
+// Reads and clears the error word (synchronises s unless it is capturing).
+cslsm_status zsweep_check(ZsweepWs &ws, cudaStream_t s);
+void zsweep_config(int enable, int force, double wait_s, int stall);
+bool zsweep_forced();  // a tiling is forced (tests): no silent per-slice path
+cslsm_status zsweep_query(int H, int W, int Z, int T, int storage, int *out8);
+int zsweep_num_candidates();
 
 // ---- BM3D (kernels_bm3d.cu) -------------------------------------------------
 struct Bm3dSlices {

@@ -62,6 +62,68 @@ __device__ __forceinline__ float2 chambolle_pair(float2 qc, float2 qn, float qr,
     return make_float2(fmaf(tau, gx0, pc.x) * i0, fmaf(tau, gx1, pc.y) * i1);
 }
 
+// chambolle_pair with every mask equal to one (a tile whose region lies inside
+// the image); multiplying by one is exact, so the results are bit-identical.
+__device__ __forceinline__ float2 chambolle_pair_interior(float2 qc, float2 qn, float qr,
+                                                          float2 pc, float tau, float2 &p2c)
+{
+    const float gx0 = qn.x - qc.x, gy0 = qc.y - qc.x;
+    const float gx1 = qn.y - qc.y, gy1 = qr - qc.y;
+    const float i0 = rcp_approx(fmaf(tau, sqrt_approx(fmaf(gx0, gx0, gy0 * gy0)), 1.f));
+    const float i1 = rcp_approx(fmaf(tau, sqrt_approx(fmaf(gx1, gx1, gy1 * gy1)), 1.f));
+    p2c = make_float2(fmaf(tau, gy0, p2c.x) * i0, fmaf(tau, gy1, p2c.y) * i1);
+    return make_float2(fmaf(tau, gx0, pc.x) * i0, fmaf(tau, gx1, pc.y) * i1);
+}
+
+// One Chambolle step on rows [r0, r1) of a band: reads p^t (A1, A2) and g
+// (sg) at rows r0-1 .. r1, writes p^{t+1} (B1, B2) at rows [r0, r1).  Arrays
+// have row pitch PW; the lane owns local columns j0, j0 + 1; gi is the image
+// row of r0 (unsigned, so rows above the image fail gi < H-1).
+template <int PW>
+__device__ __forceinline__ void tv_band_rows(const float *A1, const float *A2, const float *sg,
+                                             float *B1, float *B2, int r0, int r1, int j0,
+                                             unsigned gi, unsigned Hm1, float mc0, float mc1,
+                                             float inv_theta, float tau, int lane)
+{
+    const float *a1 = A1 + r0 * PW + j0, *a2 = A2 + r0 * PW + j0, *gg = sg + r0 * PW + j0;
+    float *b1 = B1 + r0 * PW + j0, *b2 = B2 + r0 * PW + j0;
+    float2 p1c = *reinterpret_cast<const float2 *>(a1);
+    float2 p2c = *reinterpret_cast<const float2 *>(a2);
+    float2 qc;
+    {
+        const float2 p1u = *reinterpret_cast<const float2 *>(a1 - PW);
+        const float2 gc = *reinterpret_cast<const float2 *>(gg);
+        const float p2l = reinterpret_cast<const float2 *>(a2 - 2)->y;
+        qc.x = fmaf(-gc.x, inv_theta, (p1c.x - p1u.x) + (p2c.x - p2l));
+        qc.y = fmaf(-gc.y, inv_theta, (p1c.y - p1u.y) + (p2c.y - p2c.x));
+    }
+    for (int i = r0; i < r1; ++i, ++gi) {
+        a1 += PW;
+        a2 += PW;
+        gg += PW;
+        const float2 p1n = *reinterpret_cast<const float2 *>(a1);
+        const float2 p2n = *reinterpret_cast<const float2 *>(a2);
+        const float2 gn = *reinterpret_cast<const float2 *>(gg);
+        const float p2l = reinterpret_cast<const float2 *>(a2 - 2)->y;
+        float2 qn;
+        qn.x = fmaf(-gn.x, inv_theta, (p1n.x - p1c.x) + (p2n.x - p2l));
+        qn.y = fmaf(-gn.y, inv_theta, (p1n.y - p1c.y) + (p2n.y - p2n.x));
+        const float qr = __shfl_down_sync(0xffffffffu, qc.x, 1);
+        const float mr = gi < Hm1 ? 1.f : 0.f;
+        float2 p2new = p2c;
+        const float2 p1new = chambolle_pair(qc, qn, qr, p1c, mr, mc0, mc1, tau, p2new);
+        if (lane < 31) {  // lane 31's columns belong to the next chunk
+            *reinterpret_cast<float2 *>(b1) = p1new;
+            *reinterpret_cast<float2 *>(b2) = p2new;
+        }
+        b1 += PW;
+        b2 += PW;
+        qc = qn;
+        p1c = p1n;
+        p2c = p2n;
+    }
+}
+
 // One CTA's work: the tile (bx, by) of launch slice sl.  C column chunks of 62
 // owned columns, B row bands: C * B warps; smem holds Region<C, B> arrays.
 template <int C, int B, typename S>
@@ -126,46 +188,9 @@ __device__ __forceinline__ void tv_tile_body(const TvLaunch &a, int bx, int by, 
         const int lo = s + 1, len = RH - 2 * s - 3;  // p^{s+1} rows [s+1, RH-s-2)
         const int r0 = lo + (band * len) / kBands;
         const int r1 = lo + ((band + 1) * len) / kBands;
-        if (r0 < r1) {
-            const float *a1 = A1 + r0 * PW + j0, *a2 = A2 + r0 * PW + j0, *gg = sg + r0 * PW + j0;
-            float *b1 = B1 + r0 * PW + j0, *b2 = B2 + r0 * PW + j0;
-            float2 p1c = *reinterpret_cast<const float2 *>(a1);
-            float2 p2c = *reinterpret_cast<const float2 *>(a2);
-            float2 qc;
-            {
-                const float2 p1u = *reinterpret_cast<const float2 *>(a1 - PW);
-                const float2 gc = *reinterpret_cast<const float2 *>(gg);
-                const float p2l = reinterpret_cast<const float2 *>(a2 - 2)->y;
-                qc.x = fmaf(-gc.x, inv_theta, (p1c.x - p1u.x) + (p2c.x - p2l));
-                qc.y = fmaf(-gc.y, inv_theta, (p1c.y - p1u.y) + (p2c.y - p2c.x));
-            }
-            unsigned gi = (unsigned)(gi0 + r0);
-            for (int i = r0; i < r1; ++i, ++gi) {
-                a1 += PW;
-                a2 += PW;
-                gg += PW;
-                const float2 p1n = *reinterpret_cast<const float2 *>(a1);
-                const float2 p2n = *reinterpret_cast<const float2 *>(a2);
-                const float2 gn = *reinterpret_cast<const float2 *>(gg);
-                const float p2l = reinterpret_cast<const float2 *>(a2 - 2)->y;
-                float2 qn;
-                qn.x = fmaf(-gn.x, inv_theta, (p1n.x - p1c.x) + (p2n.x - p2l));
-                qn.y = fmaf(-gn.y, inv_theta, (p1n.y - p1c.y) + (p2n.y - p2n.x));
-                const float qr = __shfl_down_sync(0xffffffffu, qc.x, 1);
-                const float mr = gi < Hm1 ? 1.f : 0.f;
-                float2 p2new = p2c;
-                const float2 p1new = chambolle_pair(qc, qn, qr, p1c, mr, mc0, mc1, tau, p2new);
-                if (lane < 31) {  // lane 31's columns belong to the next chunk
-                    *reinterpret_cast<float2 *>(b1) = p1new;
-                    *reinterpret_cast<float2 *>(b2) = p2new;
-                }
-                b1 += PW;
-                b2 += PW;
-                qc = qn;
-                p1c = p1n;
-                p2c = p2n;
-            }
-        }
+        if (r0 < r1)
+            tv_band_rows<PW>(A1, A2, sg, B1, B2, r0, r1, j0, (unsigned)(gi0 + r0), Hm1, mc0, mc1,
+                             inv_theta, tau, lane);
         __syncthreads();
         float *t1 = A1, *t2 = A2;
         A1 = B1;
