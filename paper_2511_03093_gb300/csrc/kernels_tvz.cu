@@ -403,10 +403,10 @@ struct Cfg {
 };
 
 // Row shapes (warps, rows per warp): the region is B * RPW + 2 rows high.
-constexpr int kShapes[][2] = {{16, 3}, {8, 6}, {16, 2}, {8, 4}, {12, 4}, {16, 4}};
-constexpr int kNumShapes = 6;
-constexpr int kKs[] = {4, 5, 6, 8, 10};
-constexpr int kNumK = 5;
+constexpr int kShapes[][2] = {{16, 3}, {8, 6}, {16, 2}, {8, 4}, {12, 4}, {16, 4}, {8, 16}, {16, 8}};
+constexpr int kNumShapes = 8;
+constexpr int kKs[] = {4, 5, 6, 8, 10, 20};
+constexpr int kNumK = 6;
 constexpr int kNumCand = kNumShapes * kNumK * 2;  // x target CTAs per SM (1, 2)
 
 template <int B, int RPW>
@@ -425,7 +425,9 @@ const void *kernel_of(int shape, int storage)
     case 2: return kernel_for<16, 2>(storage);
     case 3: return kernel_for<8, 4>(storage);
     case 4: return kernel_for<12, 4>(storage);
-    default: return kernel_for<16, 4>(storage);
+    case 5: return kernel_for<16, 4>(storage);
+    case 6: return kernel_for<8, 16>(storage);
+    default: return kernel_for<16, 8>(storage);
     }
 }
 
