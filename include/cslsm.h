@@ -207,12 +207,14 @@ typedef struct {
 } cslsm_batch_item;
 
 /* Create a batch over n_items items (plans on the current device) with one
- * parameter set: denoiser TV, tol 0, init_user 0, tv_inner <= 24.  b and
- * v_out pointers are recorded: every run reads and writes the same buffers,
- * and u^0 = d^0 = 0 in each run.  With cslsm_set_autotune(1) the tile rows
- * are chosen by timing one-iteration runs of a few candidates (this
- * synchronises `stream` and overwrites the items' state and v_out).
- * Synchronises `stream`. */
+ * parameter set: denoiser TV, tol 0, init_user 0.  b and v_out pointers are
+ * recorded: every run reads and writes the same buffers, and u^0 = d^0 = 0 in
+ * each run.  The TV proxes run in phases of at most 10 Chambolle steps whose
+ * tiles hand the dual field over through device memory the batch owns
+ * (4 floats per pixel of every item, and per voxel when gamma = 0).  With
+ * cslsm_set_autotune(1) the steps per phase are chosen by timing
+ * one-iteration runs of a few candidates (this synchronises `stream` and
+ * overwrites the items' state and v_out).  Synchronises `stream`. */
 cslsm_status cslsm_batch_create(cslsm_batch *batch, const cslsm_batch_item *items, int n_items,
                                 const cslsm_admm_params *params, void *stream);
 

@@ -559,11 +559,6 @@ cslsm_status cslsm_batch_create(cslsm_batch *out, const cslsm_batch_item *items,
     CHECK_ARG(prm->tol == 0.f, "the batched solver runs a fixed iteration count (tol = 0)");
     CHECK_ARG(prm->init_user == 0, "the batched solver starts from u = d = 0");
     CHECK_ARG(prm->iters >= 1, "iters must be >= 1");
-    if (prm->tv_inner > tv_max_steps_per_launch()) {
-        set_error("the batched solver runs at most %d TV steps per prox",
-                  tv_max_steps_per_launch());
-        return CSLSM_ERR_UNSUPPORTED;
-    }
     int dev = 0;
     for (int i = 0; i < n_items; ++i) {
         CHECK_ARG(items[i].plan && items[i].b && items[i].v_out, "item %d is incomplete", i);
@@ -590,7 +585,6 @@ cslsm_status cslsm_batch_create(cslsm_batch *out, const cslsm_batch_item *items,
     spec.tau = prm->tv_tau;
     spec.wait_limit_s = 4.0;
     const size_t esz = prm->storage == CSLSM_STORE_FP32 ? 4 : 2;
-    int maxH = 1;
     for (int i = 0; i < n_items; ++i) {
         const cslsm_plan_s *p = items[i].plan;
         BatchItemSpec it{};
@@ -608,20 +602,18 @@ cslsm_status cslsm_batch_create(cslsm_batch *out, const cslsm_batch_item *items,
         spec.items.push_back(it);
         bt->zero.push_back({p->u, esz * (size_t)p->g.voxels()});
         bt->zero.push_back({p->d, esz * (size_t)p->g.voxels()});
-        maxH = std::max(maxH, p->g.H);
     }
-    // tile rows: the largest region that fits (least halo work) unless timing
-    // a few candidates on the batch itself is asked for (autotune mode 1)
-    const int rows_max = std::max(2, std::min(batch_max_tile_rows(T), maxH));
-    int rows = rows_max;
-    if (tv_get_mode() == 1) {
+    // steps per phase: a fixed default unless timing a few candidates on the
+    // batch itself is asked for (autotune mode 1)
+    int kbest = std::min(std::max(T, 1), 10);
+    if (tv_get_mode() == 1 && T > 0) {
         float best = 1e30f;
-        const int cand[] = {rows_max, 32, 24, 16};
+        const int cand[] = {7, 10, 14, 20};
         for (int c : cand) {
-            if (c > rows_max) continue;
+            if (c > T) continue;
             BatchSpec trial = spec;
             trial.iters = 1;
-            for (auto &it : trial.items) it.TH = c;
+            trial.k = c;
             cslsm_batch_s probe;
             probe.device = dev;
             probe.zero = bt->zero;
@@ -648,11 +640,11 @@ cslsm_status cslsm_batch_create(cslsm_batch *out, const cslsm_batch_item *items,
             }
             if (ms < best) {
                 best = ms;
-                rows = c;
+                kbest = c;
             }
         }
     }
-    for (auto &it : spec.items) it.TH = rows;
+    spec.k = kbest;
     st = build_and_capture(bt, spec);
     if (st) {
         free_batch(bt);

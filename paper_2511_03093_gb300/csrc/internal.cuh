@@ -176,11 +176,11 @@ struct BatchItemSpec {
     const uint32_t *words;
     int wstride;
     int H, W, N, R;
-    int TH;           // TV tile rows (tile columns follow from the steps)
 };
 struct BatchSpec {
     std::vector<BatchItemSpec> items;
     int iters, T, storage, stall_test;
+    int k;  // Chambolle steps per phase (the TV tiles trade p through L2 between phases)
     float rho, lam, gamma, tau;
     double wait_limit_s;
 };
@@ -193,7 +193,6 @@ struct BatchRun {
     size_t smem = 0;
     int grid = 0, storage = 0;
 };
-int batch_max_tile_rows(int T);
 
 // ---- differentiable unrolled solver (kernels_diff.cu) -------------------------
 size_t unrolled_workspace_bytes(int B, int Z, int H, int W, int T, int S);

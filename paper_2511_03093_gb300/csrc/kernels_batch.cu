@@ -3,13 +3,22 @@
 // persistent kernel launch, captured once in a CUDA graph and replayed.
 //
 // Work decomposition.  For every item (measurement) an iteration is a chain of
-// phases: the x-update (Eq. v-update, units of 1024 pixel columns), then the
-// TV u-step (units = tiles of one slice; with gamma > 0 one phase per slice
-// in Gauss-Seidel order, otherwise one phase holding every slice's tiles).
-// Units of a phase are independent; a phase may start when every unit of the
-// item's previous phase is done.  All units of all items and iterations are
-// numbered in one global order: iteration-major, then phase level, then item
-// - so every unit a unit waits for has a smaller number.
+// phases: the x-update (Eq. v-update, units of 512 pixel columns), then the
+// TV u-step cut into phases of at most k Chambolle steps.  A TV unit is one
+// tile of one slice for one phase: it forms g on its region (the tile plus a
+// halo of k + 1 pixels; with gamma > 0 from the newest u_{n-1} and the previous
+// u_{n+1}, Sec. III-C), loads the dual field p that the previous phase left in
+// the item's L2-resident exchange buffer (p = 0 in the first phase), runs the
+// steps with the dual field of every warp's rows in registers, and stores p of
+// its own tile for the next phase, or, in the last phase, u = g - theta div p
+// and d = w - u.  With gamma > 0 the slices follow one another in
+// Gauss-Seidel order (one level per slice and phase); with gamma = 0 a level
+// holds one phase of every slice.  Units of a level are independent; a level
+// may start when every unit of the item's previous levels is done.  All units
+// of all items and iterations are numbered in one global order: iteration-
+// major, then level, then item - so every unit a unit waits for has a smaller
+// number.  Many items in flight hide the exchange latency that bounds the
+// single-volume sweep.
 //
 // Scheduling.  The grid is exactly as many CTAs as fit on the GPU at once.
 // Each CTA takes the next unit number from a global ticket counter, waits
@@ -21,6 +30,9 @@
 // batch's error word, every CTA stops taking units, and the host reports
 // CSLSM_ERR_TIMEOUT.  Data produced inside the launch is read with L2-only
 // loads (__ldcg) after an acquire fence, never from a possibly stale L1.
+//
+// The arithmetic per pixel is that of the per-slice tile kernel and the z
+// sweep, so results are bit-identical to per-volume solves.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -34,18 +46,22 @@
 namespace cslsm {
 namespace {
 
-constexpr int kBC = 2, kBB = 16;       // TV kernel variant used by the batch
-constexpr int kBNT = kBC * kBB * 32;  // 1024 threads per CTA
+constexpr int kBW = 16, kBR = 8;     // warps per CTA, rows of the region per warp
+constexpr int kBNT = kBW * 32;       // 512 threads per CTA
+constexpr int kBRH = kBW * kBR + 2;  // region rows
+constexpr int kBPW = 64;             // region columns
 
 struct BItem {
     void *u, *d, *w;
     const float *b;
     float *v_out;
     const uint32_t *words;
+    float *pbuf;  // [2 parities][2 components][slots][H][W], slots = 1 (gamma > 0) or Z
     int wstride;
     int H, W, N, R, Z;
-    int TH, TW, RH, tiles_x, tiles;
+    int hh, TH, TW, tiles_x, tiles;
     int units_x;
+    long long units_lvl;  // TV units per level
     long long units_iter;
 };
 
@@ -63,7 +79,7 @@ struct BDesc {
     long long timeout_ns;
     int stall_test;
     float rho, lam, gam, tau;
-    int T;
+    int T, k, P;  // steps per prox, steps per phase, phases per prox
 };
 
 __device__ __forceinline__ unsigned long long global_ns()
@@ -73,11 +89,10 @@ __device__ __forceinline__ unsigned long long global_ns()
     return t;
 }
 
-// Units of item it before phase p of an iteration.
-__device__ __forceinline__ long long phase_prefix(const BItem &it, int p, bool zsweep)
+// Units of item it before level p of an iteration.
+__device__ __forceinline__ long long level_prefix(const BItem &it, int p)
 {
-    if (p == 0) return 0;
-    return it.units_x + (zsweep ? (long long)(p - 1) * it.tiles : 0);
+    return p == 0 ? 0 : it.units_x + (long long)(p - 1) * it.units_lvl;
 }
 
 template <typename S>
@@ -110,10 +125,176 @@ __device__ void xupdate_unit(const BItem &it, int unit, float rho, bool last)
     }
 }
 
+// Phase j (of D.P) of slice n's TV prox on tile `tile` of item it: g on the
+// region, p from the previous phase (or 0), ns Chambolle steps with the rows
+// in registers, then p of the own tile (or the final u, d) back to memory.
 template <typename S>
-__global__ void __launch_bounds__(kBNT, 1) batch_persistent_kernel(const BDesc *__restrict__ dp)
+__device__ void tv_unit(const BItem &it, const BDesc &D, int n, int j, int tile, Bnd<kBW> &sb)
 {
-    extern __shared__ float smem[];
+    constexpr unsigned FULL = 0xffffffffu;
+    constexpr int B = kBW, RPW = kBR, NR = kBR + 1, RH = kBRH;
+    const int H = it.H, W = it.W, hh = it.hh, TH = it.TH, TW = it.TW;
+    const int bx = tile % it.tiles_x, by = tile / it.tiles_x;
+    const int gi0 = by * TH - hh, gj0 = bx * TW - hh;
+    const size_t HW = (size_t)H * W;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const int j0 = 2 * lane, r0 = 1 + wp * RPW, gc = gj0 + j0;
+    const float mc0 = (gc >= 0 && gc < W - 1) ? 1.f : 0.f;
+    const float mc1 = (gc + 1 >= 0 && gc + 1 < W - 1) ? 1.f : 0.f;
+    const bool inc[2] = {gc >= 0 && gc < W, gc + 1 >= 0 && gc + 1 < W};
+    const bool ownc[2] = {inc[0] && j0 >= hh && j0 < hh + TW,
+                          inc[1] && j0 + 1 >= hh && j0 + 1 < hh + TW};
+    const bool interior = gi0 >= 0 && gi0 + RH < H && gj0 >= 0 && gj0 + kBPW < W;
+    const unsigned Hm1 = (unsigned)(H - 1);
+    float mr[RPW];
+    int off[NR];
+    unsigned inm = 0, ownm = 0;
+#pragma unroll
+    for (int i = 0; i < NR; ++i) {
+        const int gi = gi0 + r0 + i;
+        const bool inr = gi >= 0 && gi < H;
+        off[i] = gi * W + gc;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            if (inr && inc[c]) inm |= 1u << (2 * i + c);
+            if (i < RPW && inr && ownc[c] && r0 + i >= hh && r0 + i < hh + TH)
+                ownm |= 1u << (2 * i + c);
+        }
+        if (i < RPW) mr[i] = (unsigned)gi < Hm1 ? 1.f : 0.f;
+    }
+    const float gam = it.Z > 1 ? D.gam : 0.f;
+    const float rho = D.rho, inv_rho2g = 1.f / (D.rho + 2.f * gam);
+    const float theta = D.lam / (D.rho + 2.f * gam);
+    const float inv_theta = theta > 0.f ? 1.f / theta : 0.f;
+    const S *wn = (const S *)it.w + (size_t)n * HW;
+    const S *um = (const S *)it.u + (size_t)((n + it.Z - 1) % it.Z) * HW;
+    const S *up = (const S *)it.u + (size_t)((n + 1) % it.Z) * HW;
+
+    float2 g[RPW], gdn;
+    {
+        float gv[2 * NR];
+#pragma unroll
+        for (int q = 0; q < 2 * NR; ++q) {
+            gv[q] = 0.f;
+            if (inm & (1u << q)) {
+                const size_t o = (size_t)(off[q >> 1] + (q & 1));
+                const float wv = ld_l2<S>(wn + o);
+                gv[q] = gam > 0.f ? (rho * wv + gam * (ld_l2<S>(um + o) + ld_l2<S>(up + o))) *
+                                        inv_rho2g
+                                  : wv;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < RPW; ++i) g[i] = make_float2(gv[2 * i], gv[2 * i + 1]);
+        gdn = make_float2(gv[2 * RPW], gv[2 * RPW + 1]);
+    }
+    const int Zp = gam > 0.f ? 1 : it.Z, slot = gam > 0.f ? 0 : n;
+    float2 p1[RPW], p2[RPW];
+    float2 f1 = make_float2(0.f, 0.f), f2 = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < RPW; ++i) {
+        p1[i] = make_float2(0.f, 0.f);
+        p2[i] = make_float2(0.f, 0.f);
+    }
+    if (j > 0) {
+        const float *P1 = it.pbuf + ((size_t)((j - 1) & 1) * 2 * Zp + slot) * HW;
+        const float *P2 = P1 + (size_t)Zp * HW;
+#pragma unroll
+        for (int i = 0; i < RPW; ++i) {
+            if (inm & (1u << (2 * i))) {
+                p1[i].x = __ldcg(P1 + off[i]);
+                p2[i].x = __ldcg(P2 + off[i]);
+            }
+            if (inm & (1u << (2 * i + 1))) {
+                p1[i].y = __ldcg(P1 + off[i] + 1);
+                p2[i].y = __ldcg(P2 + off[i] + 1);
+            }
+        }
+        if (wp == 0 || wp == B - 1) {  // frozen rows 0 and RH - 1 of the region
+            const int gi = gi0 + (wp == 0 ? 0 : RH - 1);
+            if (gi >= 0 && gi < H) {
+                const size_t o = (size_t)gi * W + gc;
+                if (inc[0]) {
+                    f1.x = __ldcg(P1 + o);
+                    f2.x = __ldcg(P2 + o);
+                }
+                if (inc[1]) {
+                    f1.y = __ldcg(P1 + o + 1);
+                    f2.y = __ldcg(P2 + o + 1);
+                }
+            }
+        }
+    }
+    if (wp == 0) {
+        sb.up[0][0][lane] = f1;
+        sb.up[1][0][lane] = f1;
+    }
+    if (wp == B - 1) {
+        sb.dn1[0][B - 1][lane] = f1;
+        sb.dn1[1][B - 1][lane] = f1;
+        sb.dn2[0][B - 1][lane] = f2;
+        sb.dn2[1][B - 1][lane] = f2;
+    }
+    if (wp + 1 < B) sb.up[0][wp + 1][lane] = p1[RPW - 1];
+    if (wp > 0) {
+        sb.dn1[0][wp - 1][lane] = p1[0];
+        sb.dn2[0][wp - 1][lane] = p2[0];
+    }
+    __syncthreads();
+    const int ns = min(D.k, D.T - j * D.k);
+    if (interior)
+        sweep_steps<true, B, RPW>(sb, p1, p2, g, gdn, mr, mc0, mc1, inv_theta, D.tau, ns, wp,
+                                  lane);
+    else
+        sweep_steps<false, B, RPW>(sb, p1, p2, g, gdn, mr, mc0, mc1, inv_theta, D.tau, ns, wp,
+                                   lane);
+    if (j < D.P - 1) {  // p of the own tile for the next phase
+        float *Q1 = it.pbuf + ((size_t)(j & 1) * 2 * Zp + slot) * HW;
+        float *Q2 = Q1 + (size_t)Zp * HW;
+#pragma unroll
+        for (int i = 0; i < RPW; ++i) {
+            if (ownm & (1u << (2 * i))) {
+                Q1[off[i]] = p1[i].x;
+                Q2[off[i]] = p2[i].x;
+            }
+            if (ownm & (1u << (2 * i + 1))) {
+                Q1[off[i] + 1] = p1[i].y;
+                Q2[off[i] + 1] = p2[i].y;
+            }
+        }
+    } else {  // u_n = g - theta div p^T and d_n = w_n - u_n on the own tile
+        S *un = (S *)it.u + (size_t)n * HW;
+        S *dn = (S *)it.d + (size_t)n * HW;
+        const float2 pu0 = sb.up[ns & 1][wp][lane];
+        float wv[RPW][2];
+#pragma unroll
+        for (int i = 0; i < RPW; ++i)
+#pragma unroll
+            for (int c = 0; c < 2; ++c)
+                wv[i][c] =
+                    (ownm & (1u << (2 * i + c))) ? ld_l2<S>(wn + (size_t)off[i] + c) : 0.f;
+#pragma unroll
+        for (int i = 0; i < RPW; ++i) {
+            const float p2l = __shfl_up_sync(FULL, p2[i].y, 1);
+            const float2 pu = i == 0 ? pu0 : p1[i - 1];
+            const float dx = (p1[i].x - pu.x) + (p2[i].x - p2l);
+            const float dy = (p1[i].y - pu.y) + (p2[i].y - p2[i].x);
+            const float uu[2] = {g[i].x - theta * dx, g[i].y - theta * dy};
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                if (!(ownm & (1u << (2 * i + c)))) continue;
+                const size_t o = (size_t)off[i] + c;
+                st<S>(un + o, uu[c]);
+                st<S>(dn + o, wv[i][c] - rnd<S>(uu[c]));
+            }
+        }
+    }
+}
+
+template <typename S>
+__global__ void __launch_bounds__(kBNT) batch_persistent_kernel(const BDesc *__restrict__ dp)
+{
+    __shared__ Bnd<kBW> sb;
     __shared__ long long s_t;
     __shared__ int s_abort;
     const BDesc D = *dp;
@@ -146,12 +327,12 @@ __global__ void __launch_bounds__(kBNT, 1) batch_persistent_kernel(const BDesc *
         const int i = D.ent_item[e0];
         const int unit = (int)(r - D.ent_cum[e0]);
         const BItem &it = D.items[i];
-        // wait for the item's previous phase (and iteration)
+        // wait for the item's previous levels (and iteration)
         if (threadIdx.x == 0) {
             const unsigned long long need =
                 D.stall_test ? ~0ull
                              : (unsigned long long)((long long)k * it.units_iter +
-                                                    phase_prefix(it, p, zsweep));
+                                                    level_prefix(it, p));
             const unsigned long long t0 = global_ns();
             while (*(volatile unsigned long long *)(D.done + i) < need) {
                 if (*(volatile int *)D.error) {
@@ -163,7 +344,7 @@ __global__ void __launch_bounds__(kBNT, 1) batch_persistent_kernel(const BDesc *
                     s_abort = 1;
                     break;
                 }
-                __nanosleep(256);
+                __nanosleep(128);
             }
             __threadfence();
         }
@@ -172,35 +353,19 @@ __global__ void __launch_bounds__(kBNT, 1) batch_persistent_kernel(const BDesc *
         if (p == 0) {
             xupdate_unit<S>(it, unit, D.rho, k == D.iters - 1);
         } else {
-            TvLaunch a{};
-            a.w = it.w;
-            a.u = it.u;
-            a.d = it.d;
-            a.H = it.H;
-            a.W = it.W;
-            a.Z = it.Z;
-            a.T = D.lam > 0.f ? D.T : 0;
-            a.TH = it.TH;
-            a.TW = it.TW;
-            a.RH = it.RH;
-            a.rho = D.rho;
-            a.gamma = it.Z > 1 ? D.gam : 0.f;
-            a.inv_rho2g = 1.f / (D.rho + 2.f * a.gamma);
-            a.theta = D.lam / (D.rho + 2.f * a.gamma);
-            a.inv_theta = a.theta > 0.f ? 1.f / a.theta : 0.f;
-            a.tau = D.tau;
-            a.write_final = 1;
-            a.n0 = 0;
-            a.nslices = 1;
-            int n, tile;
-            if (zsweep) {
-                n = p - 1;
+            // level p: slice n, phase j (gamma > 0), or phase j of every slice
+            const int q = p - 1;
+            int n, j, tile;
+            if (zsweep && it.Z > 1) {
+                n = q / D.P;
+                j = q - n * D.P;
                 tile = unit;
             } else {
+                j = q;
                 n = unit / it.tiles;
                 tile = unit - n * it.tiles;
             }
-            tv_tile_body<kBC, kBB, S>(a, tile % it.tiles_x, tile / it.tiles_x, n, smem);
+            tv_unit<S>(it, D, n, j, tile, sb);
         }
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -211,39 +376,40 @@ __global__ void __launch_bounds__(kBNT, 1) batch_persistent_kernel(const BDesc *
 }
 
 template <typename S>
-cslsm_status launch_persistent(const BDesc *dp, int grid, size_t smem, cudaStream_t s)
+cslsm_status launch_persistent(const BDesc *dp, int grid, cudaStream_t s)
 {
     LaunchScope ls(K_BATCH, s);
-    batch_persistent_kernel<S><<<grid, kBNT, smem, s>>>(dp);
+    batch_persistent_kernel<S><<<grid, kBNT, 0, s>>>(dp);
     CSLSM_LAUNCHED();
     return CSLSM_OK;
 }
 
 template <typename S>
-cslsm_status occupancy(size_t smem, int &per_sm)
+cslsm_status occupancy(int &per_sm)
 {
-    CSLSM_CUDA(cudaFuncSetAttribute(batch_persistent_kernel<S>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     CSLSM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_persistent_kernel<S>,
-                                                             kBNT, smem));
+                                                             kBNT, 0));
     return CSLSM_OK;
 }
 
 }  // namespace
 
-int batch_max_tile_rows(int T)
-{
-    // the largest region that fits: 5 arrays of 64 C x RH floats in 227 KB
-    const int rh = (int)((227 * 1024 / sizeof(float) / 5 - 4) / (64 * kBC));
-    return std::max(0, rh - 2 * T - 2);
-}
-
 cslsm_status batch_build(const BatchSpec &spec, BatchRun &run)
 {
     const int n = (int)spec.items.size();
     const bool zs = spec.gamma > 0.f;
+    const int T = spec.lam > 0.f ? spec.T : 0;
+    const int k = T > 0 ? std::max(1, std::min(spec.k, T)) : 0;
+    const int P = T > 0 ? (T + k - 1) / k : 1;
+    const int hh = k + 1;
+    if (kBRH - 2 * hh < 1 || kBPW - 2 * hh < 1) {
+        set_error("batched TV: %d steps per phase leave no tile", k);
+        return CSLSM_ERR_UNSUPPORTED;
+    }
     std::vector<BItem> items(n);
-    int levels = 1, max_rh = 0;
+    int levels = 1;
+    size_t pbytes = 0;
+    std::vector<size_t> poff(n);
     for (int i = 0; i < n; ++i) {
         const BatchItemSpec &s = spec.items[i];
         BItem &b = items[i];
@@ -259,18 +425,22 @@ cslsm_status batch_build(const BatchSpec &spec, BatchRun &run)
         b.N = s.N;
         b.R = s.R;
         b.Z = s.N * s.R;
-        const int T = spec.lam > 0.f ? spec.T : 0;
-        b.TH = s.TH;
-        b.RH = s.TH + 2 * T + 2;
-        b.TW = 62 * kBC + 2 - 2 * T - 2;
+        b.hh = hh;
+        b.TH = kBRH - 2 * hh;
+        b.TW = kBPW - 2 * hh;
         b.tiles_x = (s.W + b.TW - 1) / b.TW;
         b.tiles = b.tiles_x * ((s.H + b.TH - 1) / b.TH);
         b.units_x = (s.H * s.W + kBNT - 1) / kBNT;
-        b.units_iter = b.units_x + (long long)b.tiles * b.Z;
-        levels = std::max(levels, zs ? 1 + b.Z : 2);
-        max_rh = std::max(max_rh, b.RH);
+        const bool chain = zs && b.Z > 1;  // Gauss-Seidel: one level per slice and phase
+        b.units_lvl = chain ? b.tiles : (long long)b.tiles * b.Z;
+        const int lv = chain ? b.Z * P : P;
+        b.units_iter = b.units_x + b.units_lvl * lv;
+        levels = std::max(levels, 1 + lv);
+        poff[i] = pbytes;
+        if (P > 1) pbytes += (4 * (size_t)(chain ? 1 : b.Z) * s.H * s.W * sizeof(float) + 255) &
+                             ~size_t(255);
     }
-    // level tables: per level p, the items having phase p and their unit counts
+    // level tables: per level p, the items having level p and their unit counts
     std::vector<long long> level_cum(levels + 1, 0);
     std::vector<int> lvl_start(levels + 1, 0), ent_item;
     std::vector<long long> ent_cum;
@@ -279,10 +449,8 @@ cslsm_status batch_build(const BatchSpec &spec, BatchRun &run)
         long long acc = 0;
         for (int i = 0; i < n; ++i) {
             const BItem &b = items[i];
-            long long c = 0;
-            if (p == 0) c = b.units_x;
-            else if (zs) c = (p - 1 < b.Z) ? b.tiles : 0;
-            else c = (p == 1) ? (long long)b.tiles * b.Z : 0;
+            const long long lv = (b.units_iter - b.units_x) / b.units_lvl;
+            const long long c = p == 0 ? b.units_x : (p - 1 < lv ? b.units_lvl : 0);
             if (c == 0) continue;
             ent_item.push_back(i);
             ent_cum.push_back(acc);
@@ -292,13 +460,15 @@ cslsm_status batch_build(const BatchSpec &spec, BatchRun &run)
     }
     lvl_start[levels] = (int)ent_item.size();
     const long long units_iter = level_cum[levels];
-    // one device allocation for descriptors, tables and counters
+    // one device allocation for descriptors, tables, counters and the items'
+    // dual-field exchange buffers
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
     const size_t sz_items = al(sizeof(BItem) * n), sz_lc = al(sizeof(long long) * (levels + 1)),
                  sz_ls = al(sizeof(int) * (levels + 1)), sz_ei = al(sizeof(int) * ent_item.size()),
                  sz_ec = al(sizeof(long long) * ent_cum.size()), sz_cnt = al(8 * (n + 1)),
                  sz_err = 256, sz_desc = al(sizeof(BDesc));
-    const size_t total = sz_items + sz_lc + sz_ls + sz_ei + sz_ec + sz_cnt + sz_err + sz_desc;
+    const size_t total =
+        sz_items + sz_lc + sz_ls + sz_ei + sz_ec + sz_cnt + sz_err + sz_desc + pbytes;
     char *base = nullptr;
     CSLSM_CUDA(cudaMalloc(&base, total));
     run.mem = base;
@@ -318,6 +488,8 @@ cslsm_status batch_build(const BatchSpec &spec, BatchRun &run)
     int *d_err = (int *)q;
     q += sz_err;
     BDesc *d_desc = (BDesc *)q;
+    q += sz_desc;
+    for (int i = 0; i < n; ++i) items[i].pbuf = P > 1 ? (float *)(q + poff[i]) : nullptr;
     BDesc D{};
     D.items = d_items;
     D.n = n;
@@ -338,7 +510,9 @@ cslsm_status batch_build(const BatchSpec &spec, BatchRun &run)
     D.lam = spec.lam;
     D.gam = spec.gamma;
     D.tau = spec.tau;
-    D.T = spec.T;
+    D.T = T;
+    D.k = k;
+    D.P = P;
     CSLSM_CUDA(cudaMemcpy(d_items, items.data(), sizeof(BItem) * n, cudaMemcpyHostToDevice));
     CSLSM_CUDA(cudaMemcpy(d_lc, level_cum.data(), sizeof(long long) * (levels + 1),
                           cudaMemcpyHostToDevice));
@@ -353,16 +527,12 @@ cslsm_status batch_build(const BatchSpec &spec, BatchRun &run)
     run.counters = d_cnt;
     run.counters_bytes = 8 * (n + 1);
     run.error = d_err;
-    run.smem = tv_smem_bytes(kBC, max_rh);
-    if (run.smem > 227 * 1024) {
-        set_error("batched TV tile needs %zu bytes of shared memory", run.smem);
-        return CSLSM_ERR_UNSUPPORTED;
-    }
+    run.smem = 0;
     int per_sm = 0, dev = 0, sms = 0;
     cslsm_status e;
-    if (spec.storage == CSLSM_STORE_BF16) e = occupancy<__nv_bfloat16>(run.smem, per_sm);
-    else if (spec.storage == CSLSM_STORE_FP16) e = occupancy<__half>(run.smem, per_sm);
-    else e = occupancy<float>(run.smem, per_sm);
+    if (spec.storage == CSLSM_STORE_BF16) e = occupancy<__nv_bfloat16>(per_sm);
+    else if (spec.storage == CSLSM_STORE_FP16) e = occupancy<__half>(per_sm);
+    else e = occupancy<float>(per_sm);
     if (e) return e;
     CSLSM_CUDA(cudaGetDevice(&dev));
     CSLSM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -390,9 +560,9 @@ cslsm_status batch_enqueue(const BatchRun &run, cudaStream_t s)
     CSLSM_CUDA(cudaMemsetAsync(run.counters, 0, run.counters_bytes, s));
     CSLSM_CUDA(cudaMemsetAsync(run.error, 0, sizeof(int), s));
     const BDesc *dp = (const BDesc *)run.desc;
-    if (run.storage == CSLSM_STORE_BF16) return launch_persistent<__nv_bfloat16>(dp, run.grid, run.smem, s);
-    if (run.storage == CSLSM_STORE_FP16) return launch_persistent<__half>(dp, run.grid, run.smem, s);
-    return launch_persistent<float>(dp, run.grid, run.smem, s);
+    if (run.storage == CSLSM_STORE_BF16) return launch_persistent<__nv_bfloat16>(dp, run.grid, s);
+    if (run.storage == CSLSM_STORE_FP16) return launch_persistent<__half>(dp, run.grid, s);
+    return launch_persistent<float>(dp, run.grid, s);
 }
 
 }  // namespace cslsm

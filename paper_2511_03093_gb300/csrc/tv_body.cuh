@@ -75,6 +75,61 @@ __device__ __forceinline__ float2 chambolle_pair_interior(float2 qc, float2 qn, 
     return make_float2(fmaf(tau, gx0, pc.x) * i0, fmaf(tau, gx1, pc.y) * i1);
 }
 
+// Boundary rows exchanged between the warps of a CTA each step (double-
+// buffered by step parity): p1 of the row above warp w's rows, p1 and p2 of
+// the row below.
+template <int B>
+struct Bnd {
+    float2 up[2][B][32];
+    float2 dn1[2][B][32];
+    float2 dn2[2][B][32];
+};
+
+// ns Chambolle steps on the warp's rows (registers) with one barrier per step.
+// INTERIOR: the CTA's whole region lies inside the image, all masks are one.
+template <bool INTERIOR, int B, int RPW>
+__device__ __forceinline__ void sweep_steps(Bnd<B> &sb, float2 (&p1)[RPW], float2 (&p2)[RPW],
+                                            const float2 (&g)[RPW], float2 gdn,
+                                            const float (&mr)[RPW], float mc0, float mc1,
+                                            float inv_theta, float tau, int ns, int wp, int lane)
+{
+    constexpr unsigned FULL = 0xffffffffu;
+    for (int t = 0; t < ns; ++t) {
+        const int par = t & 1, nxt = par ^ 1;
+        const float2 pu0 = sb.up[par][wp][lane];
+        const float2 dn1 = sb.dn1[par][wp][lane], dn2 = sb.dn2[par][wp][lane];
+        float2 q[RPW + 1];
+#pragma unroll
+        for (int i = 0; i < RPW; ++i) {
+            const float p2l = __shfl_up_sync(FULL, p2[i].y, 1);
+            const float2 pu = i == 0 ? pu0 : p1[i - 1];
+            q[i].x = fmaf(-g[i].x, inv_theta, (p1[i].x - pu.x) + (p2[i].x - p2l));
+            q[i].y = fmaf(-g[i].y, inv_theta, (p1[i].y - pu.y) + (p2[i].y - p2[i].x));
+        }
+        {
+            const float p2l = __shfl_up_sync(FULL, dn2.y, 1);
+            q[RPW].x = fmaf(-gdn.x, inv_theta, (dn1.x - p1[RPW - 1].x) + (dn2.x - p2l));
+            q[RPW].y = fmaf(-gdn.y, inv_theta, (dn1.y - p1[RPW - 1].y) + (dn2.y - dn2.x));
+        }
+#pragma unroll
+        for (int i = 0; i < RPW; ++i) {
+            const float qr = __shfl_down_sync(FULL, q[i].x, 1);
+            float2 p2n = p2[i];
+            const float2 p1n =
+                INTERIOR ? chambolle_pair_interior(q[i], q[i + 1], qr, p1[i], tau, p2n)
+                         : chambolle_pair(q[i], q[i + 1], qr, p1[i], mr[i], mc0, mc1, tau, p2n);
+            p1[i] = p1n;
+            p2[i] = p2n;
+        }
+        if (wp + 1 < B) sb.up[nxt][wp + 1][lane] = p1[RPW - 1];
+        if (wp > 0) {
+            sb.dn1[nxt][wp - 1][lane] = p1[0];
+            sb.dn2[nxt][wp - 1][lane] = p2[0];
+        }
+        __syncthreads();
+    }
+}
+
 // One Chambolle step on rows [r0, r1) of a band: reads p^t (A1, A2) and g
 // (sg) at rows r0-1 .. r1, writes p^{t+1} (B1, B2) at rows [r0, r1).  Arrays
 // have row pitch PW; the lane owns local columns j0, j0 + 1; gi is the image

@@ -43,12 +43,14 @@ def _items(cs, seed0):
     return items
 
 
-@pytest.mark.parametrize("gamma,storage", [(0.2, "fp32"), (0.0, "fp32"), (0.2, "bf16")])
-def test_batch_equals_per_volume(cs, gamma, storage):
+@pytest.mark.parametrize("gamma,storage,T", [(0.2, "fp32", 20), (0.0, "fp32", 20),
+                                             (0.2, "bf16", 20), (0.2, "fp16", 7),
+                                             (0.2, "fp32", 30), (0.0, "fp32", 3)])
+def test_batch_equals_per_volume(cs, gamma, storage, T):
     import torch
 
     items = _items(cs, 500)
-    prm = cs.Params(rho=1.0, lam=0.05, gamma=gamma, iters=12, denoiser="tv", tv_inner=20,
+    prm = cs.Params(rho=1.0, lam=0.05, gamma=gamma, iters=12, denoiser="tv", tv_inner=T,
                     storage=storage)
     batch = cs.Batch(items, prm)
     batch.run()
@@ -100,7 +102,6 @@ def test_batch_wait_timeout_is_reported(cs):
 
 def test_batch_rejects_unsupported(cs):
     items = _items(cs, 800)[:1]
-    for prm in (cs.Params(denoiser="bm3d"), cs.Params(denoiser="tv", tol=1e-3),
-                cs.Params(denoiser="tv", tv_inner=30)):
+    for prm in (cs.Params(denoiser="bm3d"), cs.Params(denoiser="tv", tol=1e-3)):
         with pytest.raises(cs.CslsmError):
             cs.Batch(items, prm)
