@@ -63,6 +63,8 @@ def lib() -> ctypes.CDLL:
         L.or_tv_prox.restype = i
         L.or_psnr.argtypes = [ctypes.c_size_t, P, P]
         L.or_psnr.restype = d
+        L.or_ssim3d.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, P]
+        L.or_ssim3d.restype = d
         L.or_bm3d.argtypes = [i, i, P, d, P]
         L.or_bm3d.restype = i
         L.or_bm3d_stage.argtypes = [i, i, P, P, d, d, P]
@@ -232,6 +234,19 @@ def psnr(x, ref) -> float:
     """3D PSNR (Sec. IV): 10 log10(n V^2 / ||x-ref||^2), V = max(ref)."""
     x, ref = _f64(x), _f64(ref)
     return float(lib().or_psnr(x.size, _p(x), _p(ref)))
+
+
+def ssim3d(x, ref, return_map: bool = False):
+    """3-D SSIM (Sec. IV): mean over all voxels of the local ssim with an
+    11^3 Gaussian window (sigma 1.5) clipped to the volume and renormalised,
+    c1 = 0.01^2, c2 = 0.03^2.  x, ref: [Z, H, W] (or [H, W])."""
+    x, ref = _f64(x), _f64(ref)
+    if x.ndim == 2:
+        x, ref = x[None], ref[None]
+    Z, H, W = x.shape
+    m = np.empty_like(x) if return_map else None
+    s = float(lib().or_ssim3d(Z, H, W, _p(x), _p(ref), _p(m) if m is not None else None))
+    return (s, m) if return_map else s
 
 
 def admm(b, masks, Z: int, *, rho: float, lam: float, gamma: float = 0.0, iters: int,

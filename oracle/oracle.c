@@ -198,6 +198,81 @@ double or_psnr(size_t n, const double *x, const double *ref)
 }
 
 /* ---------------------------------------------------------------------------
+ * 3-D SSIM (Sec. IV, evaluation metrics): the local ssim of Wang et al. with
+ * means, variances and the covariance taken over an 11 x 11 x 11 Gaussian
+ * window (standard deviation 1.5) centred on every voxel, c1 = (0.01 L)^2,
+ * c2 = (0.03 L)^2 with L = 1, averaged over every voxel of the volume.  The
+ * paper does not say how the window meets the volume's faces; here it is
+ * clipped to the volume and its weights renormalised to sum to one.  The
+ * Gaussian weights and the box clipping are both separable, so the window
+ * mean of any field is three 1-D normalised passes (x, then y, then z).
+ * Variances and the covariance are the window means of x^2, y^2, x y minus
+ * the products of the window means.
+ * ------------------------------------------------------------------------- */
+#define SSIM_R 5
+
+static void ssim_pass(const double *in, double *out, int Z, int H, int W, int axis,
+                      const double *g)
+{
+    const int n = axis == 0 ? W : (axis == 1 ? H : Z);
+    const size_t stride = axis == 0 ? 1 : (axis == 1 ? (size_t)W : (size_t)H * W);
+#pragma omp parallel for if ((size_t)Z * H * W >= 16384)
+    for (int z = 0; z < Z; ++z)
+        for (int y = 0; y < H; ++y)
+            for (int x = 0; x < W; ++x) {
+                const int c = axis == 0 ? x : (axis == 1 ? y : z);
+                const size_t o = ((size_t)z * H + y) * W + x;
+                double s = 0.0, ws = 0.0;
+                for (int k = -SSIM_R; k <= SSIM_R; ++k) {
+                    const int q = c + k;
+                    if (q < 0 || q >= n) continue;
+                    s += g[k + SSIM_R] * in[(size_t)((long long)o + (long long)k * (long long)stride)];
+                    ws += g[k + SSIM_R];
+                }
+                out[o] = s / ws;
+            }
+}
+
+static void ssim_mean(const double *f, double *out, double *tmp, int Z, int H, int W,
+                      const double *g)
+{
+    ssim_pass(f, out, Z, H, W, 0, g);
+    ssim_pass(out, tmp, Z, H, W, 1, g);
+    ssim_pass(tmp, out, Z, H, W, 2, g);
+}
+
+double or_ssim3d(int Z, int H, int W, const double *x, const double *y, double *map)
+{
+    const size_t n = (size_t)Z * H * W;
+    double g[2 * SSIM_R + 1];
+    for (int k = -SSIM_R; k <= SSIM_R; ++k) g[k + SSIM_R] = exp(-(double)(k * k) / (2.0 * 1.5 * 1.5));
+    double *buf = (double *)malloc(sizeof(double) * n * 7);
+    if (!buf) return NAN;
+    double *f = buf, *tmp = buf + n, *mx = buf + 2 * n, *my = buf + 3 * n, *sxx = buf + 4 * n,
+           *syy = buf + 5 * n, *sxy = buf + 6 * n;
+    ssim_mean(x, mx, tmp, Z, H, W, g);
+    ssim_mean(y, my, tmp, Z, H, W, g);
+    for (size_t i = 0; i < n; ++i) f[i] = x[i] * x[i];
+    ssim_mean(f, sxx, tmp, Z, H, W, g);
+    for (size_t i = 0; i < n; ++i) f[i] = y[i] * y[i];
+    ssim_mean(f, syy, tmp, Z, H, W, g);
+    for (size_t i = 0; i < n; ++i) f[i] = x[i] * y[i];
+    ssim_mean(f, sxy, tmp, Z, H, W, g);
+    const double c1 = 0.01 * 0.01, c2 = 0.03 * 0.03;
+    double acc = 0.0;
+    for (size_t i = 0; i < n; ++i) {
+        const double vx = sxx[i] - mx[i] * mx[i], vy = syy[i] - my[i] * my[i];
+        const double cxy = sxy[i] - mx[i] * my[i];
+        const double s = (2.0 * mx[i] * my[i] + c1) * (2.0 * cxy + c2) /
+                         ((mx[i] * mx[i] + my[i] * my[i] + c1) * (vx + vy + c2));
+        if (map) map[i] = s;
+        acc += s;
+    }
+    free(buf);
+    return acc / (double)n;
+}
+
+/* ---------------------------------------------------------------------------
  * Algorithm 1 (CS LSM temporal reconstruction; gamma = 0 is the slice-based
  * method of Sec. III-B).  One iteration k:
  *   1. v^{k+1} by Eq. (v-update) per shot (Woodbury form above);

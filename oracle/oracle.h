@@ -15,6 +15,7 @@ void or_vupdate(int N, int R, int H, int W, const double *phi, int per_slice,
                 const double *b, const double *u, const double *d, double rho, double *v);
 int or_tv_prox(int H, int W, const double *g, double theta, int T, double tau, double *u);
 double or_psnr(size_t n, const double *x, const double *ref);
+double or_ssim3d(int Z, int H, int W, const double *x, const double *y, double *map);
 int or_bm3d(int H, int W, const double *g, double sigma, double *u);
 int or_bm3d_stage(int H, int W, const double *noisy, const double *guide, double sigma,
                   double lambda3d, double *out);
