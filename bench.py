@@ -91,6 +91,15 @@ def _traffic():
     return rec.get("dram_bytes_per_launch")
 
 
+def _quality(cs, v, data, dev):
+    """PSNR and 3-D SSIM (Sec. IV) of the last solve's v^K against the synthetic
+    ground truth, both computed by the library's kernels outside the timed region."""
+    import torch
+
+    x = torch.from_numpy(data["x"].astype("float32")).to(dev)
+    return {"psnr_db": float(cs.psnr(v, x)), "ssim3d": float(cs.ssim3d(v, x))}
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle samples while the timed region runs."""
 
@@ -340,6 +349,7 @@ def run_ours(args) -> None:
             "gpu_launches": int(launches), "clocks": clk,
             "zsweep_shape": cs.zsweep_shape(w.H, w.W, w.Z, PARAMS["tv_inner"]),
             "step_ms": [round(x, 3) for x in step_ms],
+            "quality": _quality(cs, v_d, data, dev),
         }
         print(json.dumps(out), flush=True)
     plan.close()

@@ -304,6 +304,16 @@ cslsm_status cslsm_denoise_bm3d_noalloc(const float *in, float *out, int Z, int 
  * Deterministic two-level reduction; uses a stream-ordered scratch buffer. */
 cslsm_status cslsm_psnr(const float *x, const float *ref, size_t n, double *out, void *stream);
 
+/* Volume SSIM of Sec. IV: the local ssim of Wang et al. (means, variances and
+ * covariance over an 11 x 11 x 11 Gaussian window with standard deviation 1.5,
+ * clipped to the volume and renormalised; c1 = 0.01^2, c2 = 0.03^2 for data
+ * on [0, 1]) averaged over every voxel.  x, ref: device, FP32 [Z][H][W];
+ * writes the mean as a double to out (device).  Deterministic (fixed-order
+ * FP64 reduction of FP32 local values).  Uses a stream-ordered scratch buffer
+ * of 20 bytes per voxel. */
+cslsm_status cslsm_ssim3d(const float *x, const float *ref, int Z, int H, int W, double *out,
+                          void *stream);
+
 /* Human-readable name of a status code (static string). */
 const char *cslsm_status_string(cslsm_status status);
 
@@ -367,7 +377,7 @@ unsigned long long cslsm_launch_count(void);
  * Kernel names: "pack_masks", "forward", "adjoint", "xupdate_w",
  * "tikhonov_iter", "tikhonov_prox", "tv_tile", "psnr_partials",
  * "reduce_finish", "bm3d_prep", "bm3d_match", "bm3d_filter", "bm3d_finish",
- * "batch_persistent", "unrolled", "tvz_sweep". */
+ * "batch_persistent", "unrolled", "tvz_sweep", "ssim3d". */
 cslsm_status cslsm_timing_enable(int period);
 
 /* Waits for the recorded events of `kernel` and returns how many launches

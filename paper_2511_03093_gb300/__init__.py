@@ -111,6 +111,7 @@ def lib() -> ctypes.CDLL:
                              ctypes.POINTER(AdmmStats), P],
         "cslsm_denoise": [I, P, P, I, I, I, ctypes.POINTER(AdmmParams), P],
         "cslsm_psnr": [P, P, ctypes.c_size_t, P, P],
+        "cslsm_ssim3d": [P, P, I, I, I, P, P],
         "cslsm_bm3d_match": [P, I, I, I, I, P, P, P],
         "cslsm_bm3d_stage": [I, P, P, P, I, I, I, F, P],
     }
@@ -293,6 +294,18 @@ def psnr(x: torch.Tensor, ref: torch.Tensor, stream=None) -> torch.Tensor:
     _check(lib().cslsm_psnr(_dev(x, "x", torch.float32), _dev(ref, "ref", torch.float32),
                             x.numel(), ctypes.c_void_p(out.data_ptr()), _stream(stream)),
            "cslsm_psnr")
+    return out
+
+
+def ssim3d(x: torch.Tensor, ref: torch.Tensor, stream=None) -> torch.Tensor:
+    """Volume SSIM of Sec. IV (cslsm_ssim3d) as a 0-dim float64 CUDA tensor."""
+    if x.dim() == 2:
+        x, ref = x[None], ref[None]
+    Z, H, W = x.shape
+    out = torch.empty((), dtype=torch.float64, device=x.device)
+    _check(lib().cslsm_ssim3d(_dev(x, "x", torch.float32), _dev(ref, "ref", torch.float32,
+                                                                (Z, H, W)),
+                              Z, H, W, out.data_ptr(), _stream(stream)), "cslsm_ssim3d")
     return out
 
 

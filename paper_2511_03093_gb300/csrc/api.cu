@@ -843,4 +843,20 @@ cslsm_status cslsm_psnr(const float *x, const float *ref, size_t n, double *out,
     return st;
 }
 
+cslsm_status cslsm_ssim3d(const float *x, const float *ref, int Z, int H, int W, double *out,
+                          void *stream)
+{
+    CHECK_ARG(x != nullptr && ref != nullptr && out != nullptr, "x, ref, out must be non-NULL");
+    CHECK_ARG(Z >= 1 && H >= 1 && W >= 1, "Z, H, W must be >= 1");
+    CHECK_ARG((long long)Z * H * W < (1ll << 31), "Z*H*W must be < 2^31");
+    cudaStream_t s = as_stream(stream);
+    int nb = 0;
+    const size_t bytes = ssim3d_workspace_bytes(Z, H, W, &nb);
+    void *ws = nullptr;
+    CSLSM_CUDA(cudaMallocAsync(&ws, bytes, s));
+    cslsm_status st = launch_ssim3d(x, ref, Z, H, W, ws, nb, out, s);
+    cudaFreeAsync(ws, s);
+    return st;
+}
+
 }  // extern "C"

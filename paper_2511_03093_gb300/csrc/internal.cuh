@@ -31,7 +31,7 @@ void set_error(const char *fmt, ...);
 enum KernelId {
     K_PACK = 0, K_FORWARD, K_ADJOINT, K_XUPDATE, K_TIK_ITER, K_TIK_PROX, K_TV_TILE, K_PSNR,
     K_REDUCE, K_BM3D_PREP, K_BM3D_MATCH, K_BM3D_FILTER, K_BM3D_FINISH, K_BATCH, K_DIFF, K_TVZ,
-    K_COUNT
+    K_SSIM, K_COUNT
 };
 
 // Wrap every kernel launch: counts it and, when timing is on, records CUDA
@@ -147,6 +147,13 @@ void zsweep_config(int enable, int force, double wait_s, int stall);
 bool zsweep_forced();  // a tiling is forced (tests): no silent per-slice path
 cslsm_status zsweep_query(int H, int W, int Z, int T, int storage, int *out8);
 int zsweep_num_candidates();
+
+// ---- 3-D SSIM (kernels_ssim.cu) ---------------------------------------------
+// Scratch bytes of one call (five FP32 planes of the volume and the block
+// partials); *nblocks receives the partial count launch_ssim3d expects.
+size_t ssim3d_workspace_bytes(int Z, int H, int W, int *nblocks);
+cslsm_status launch_ssim3d(const float *x, const float *ref, int Z, int H, int W, void *ws,
+                           int nblocks, double *out, cudaStream_t s);
 
 // ---- BM3D (kernels_bm3d.cu) -------------------------------------------------
 struct Bm3dSlices {
