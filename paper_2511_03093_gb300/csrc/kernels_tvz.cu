@@ -151,6 +151,7 @@ __global__ void __launch_bounds__(B * 32) tvz_sweep_kernel(const ZsArgs a)
     if (threadIdx.x == 0) s_abort = 0;
 
     float2 p1[RPW], p2[RPW], g[RPW], gdn;
+    float2 wo[RPW];  // w_n of the warp's rows, kept for d_n = w_n - u_n at the slice end
     for (int n = 0; n < a.Z; ++n) {
         const S *wn = (const S *)a.w + (size_t)n * HW;
         const S *um = (const S *)a.u + (size_t)((n + a.Z - 1) % a.Z) * HW;
@@ -215,6 +216,7 @@ __global__ void __launch_bounds__(B * 32) tvz_sweep_kernel(const ZsArgs a)
                 }
 #pragma unroll
                 for (int i = 0; i < RPW; ++i) {
+                    wo[i] = p1[i];
                     p1[i] = make_float2(0.f, 0.f);
                     p2[i] = make_float2(0.f, 0.f);
                 }
@@ -304,13 +306,6 @@ __global__ void __launch_bounds__(B * 32) tvz_sweep_kernel(const ZsArgs a)
                 S *un = (S *)a.u + (size_t)n * HW;
                 S *dn = a.d ? (S *)a.d + (size_t)n * HW : nullptr;
                 const float2 pu0 = sb.up[ns & 1][wp][lane];
-                float wv[RPW][2];
-#pragma unroll
-                for (int i = 0; i < RPW; ++i)
-#pragma unroll
-                    for (int c = 0; c < 2; ++c)
-                        wv[i][c] = (dn && ownr[i] && ownc[c]) ? ld_l2<S>(wn + (size_t)off[i] + c)
-                                                              : 0.f;
 #pragma unroll
                 for (int i = 0; i < RPW; ++i) {
                     const float p2l = __shfl_up_sync(FULL, p2[i].y, 1);
@@ -321,11 +316,11 @@ __global__ void __launch_bounds__(B * 32) tvz_sweep_kernel(const ZsArgs a)
                     const float uy = g[i].y - a.theta * dy;
                     if (ownr[i] && ownc[0]) {
                         st<S>(un + (size_t)off[i], ux);
-                        if (dn) st<S>(dn + (size_t)off[i], wv[i][0] - rnd<S>(ux));
+                        if (dn) st<S>(dn + (size_t)off[i], wo[i].x - rnd<S>(ux));
                     }
                     if (ownr[i] && ownc[1]) {
                         st<S>(un + (size_t)off[i] + 1, uy);
-                        if (dn) st<S>(dn + (size_t)off[i] + 1, wv[i][1] - rnd<S>(uy));
+                        if (dn) st<S>(dn + (size_t)off[i] + 1, wo[i].y - rnd<S>(uy));
                     }
                 }
             }
