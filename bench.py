@@ -329,7 +329,11 @@ def run_ours(args) -> None:
         roof = None
         if n_dom:
             avg_s = ms_dom / n_dom / 1e3
-            achieved = w.Z * tv_flops_per_launch(w.H, w.W, PARAMS["tv_inner"]) / avg_s / 1e12
+            # the dominant kernel's launches per solve: one per iteration, or one
+            # for the whole solve; its TV work per launch follows
+            per_step = n_dom * TIMING_PERIOD / args.steps
+            achieved = (PARAMS["iters"] * w.Z * tv_flops_per_launch(w.H, w.W, PARAMS["tv_inner"])
+                        / per_step / avg_s / 1e12)
             peak = alu_peak_tflops(sm_max)
             roof = {"bound": "alu", "kernel": DOMINANT, "achieved": achieved, "peak": peak,
                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": _traffic(),
@@ -516,6 +520,29 @@ def run_secondary(args) -> None:
         out.update(metric="unrolled PnP-ADMM voxel-iterations/s (forward + backward)", unit=UNIT,
                    value=vox * 30 / ((np.mean(fw) + np.mean(bw)) / 1e3), forward_ms=float(np.mean(fw)),
                    backward_ms=float(np.mean(bw)), batch=B, volume=[Z, H, W], iterations=30)
+    elif name == "cr_sweep_256x256x40":
+        # compression-ratio sweep: the same 40-slice volume seen through N shots of
+        # R planes each (R = Z / N in {5, 10, 20}), patterns shared by all shots
+        Z, H, W = 40, 256, 256
+        cs.set_autotune(1)
+        rows = []
+        for R in (5, 10, 20):
+            N = Z // R
+            wk = synth.Workload(f"cr{R}", Z, H, W, n_shots=N, per_slice_masks=False, drift=True,
+                                mask_p=0.5, peak=200.0, sigma_g=0.01, seed=5000 + R)
+            data = synth.generate(wk)
+            plan = cs.Plan(H, W, N, R, torch.from_numpy(data["masks"]).to(dev), per_slice=False)
+            b = torch.from_numpy(data["b"]).to(dev)
+            v = torch.empty((Z, H, W), dtype=torch.float32, device=dev)
+            prm = cs.Params(rho=1.0, lam=0.05, gamma=0.2, iters=100, denoiser="tv", tv_inner=20)
+            ms = _timed(lambda: plan.solve(b, prm, v_out=v), max(1, args.steps), 1, flush)
+            x = torch.from_numpy(data["x"].astype(np.float32)).to(dev)
+            rows.append({"R": R, "shots": N, "ms_per_solve": sum(ms) / len(ms),
+                         "voxel_it_per_s": Z * H * W * 100 / (sum(ms) / len(ms) / 1e3),
+                         "psnr_db": float(cs.psnr(v, x)), "ssim3d": float(cs.ssim3d(v, x))})
+            plan.close()
+        out.update(metric=METRIC, unit=UNIT, value=rows[0]["voxel_it_per_s"], iterations=100,
+                   volume=[Z, H, W], sweep=rows)
     else:
         raise SystemExit(f"unknown workload {name}")
     print(json.dumps(out), flush=True)
@@ -529,7 +556,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=None,
                     help="secondary workload: tikhonov_1024x1024x32, tv_1024x1024x32, "
-                         "bm3d_1024x1024x32, tv_128x128x8, batched_64, unrolled_b8")
+                         "bm3d_1024x1024x32, tv_128x128x8, batched_64, unrolled_b8, "
+                         "cr_sweep_256x256x40")
     args = ap.parse_args()
     if args.workload:
         run_secondary(args)
