@@ -93,7 +93,7 @@ __device__ __forceinline__ void block_sum2(double &a, double &c)
 //   g_r = u_r - d_r,  e = (b_j - sum_r phi_r g_r) / (rho + popc),
 //   v_r = g_r + phi_r e,  w_r = v_r + d_r.
 template <int RMAX, typename S>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, RMAX >= 32 ? 2 : 4)
 xupdate_w_kernel(const S *__restrict__ u, const S *__restrict__ d,
                  const float *__restrict__ b, const uint32_t *__restrict__ words, int wstride,
                  int HW, int R, float rho, S *__restrict__ w, float *__restrict__ v_out,
