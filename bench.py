@@ -520,6 +520,34 @@ def run_secondary(args) -> None:
         out.update(metric="unrolled PnP-ADMM voxel-iterations/s (forward + backward)", unit=UNIT,
                    value=vox * 30 / ((np.mean(fw) + np.mean(bw)) / 1e3), forward_ms=float(np.mean(fw)),
                    backward_ms=float(np.mean(bw)), batch=B, volume=[Z, H, W], iterations=30)
+    elif name == "tol_caps_512x512x16":
+        # the paper's stopping caps (Sec. IV-B): 100 iterations / 1e-3, 200 / 1e-2,
+        # checked on the device every iteration, TV + z on the benchmark volume
+        wk = synth.WORKLOADS["tvz_512x512x16"]
+        data = synth.generate(wk)
+        plan = cs.Plan(wk.H, wk.W, 1, wk.Z, torch.from_numpy(data["masks"]).to(dev))
+        b = torch.from_numpy(data["b"]).to(dev)
+        v = torch.empty((wk.Z, wk.H, wk.W), dtype=torch.float32, device=dev)
+        x = torch.from_numpy(data["x"].astype(np.float32)).to(dev)
+        cs.set_autotune(1)
+        rows = []
+        for iters, tol in ((100, 1e-3), (200, 1e-2)):
+            prm = cs.Params(rho=1.0, lam=0.05, gamma=0.2, iters=iters, tol=tol, check_every=1,
+                            denoiser="tv", tv_inner=20)
+            st = {}
+
+            def run():
+                st.update(plan.solve(b, prm, v_out=v, stats=True)[1])
+
+            ms = _timed(run, max(1, args.steps), 1, flush)
+            rows.append({"iters_cap": iters, "tol": tol, "iters_done": st["iters_done"],
+                         "rel_change": st["rel_change"], "ms_per_solve": sum(ms) / len(ms),
+                         "psnr_db": float(cs.psnr(v, x)), "ssim3d": float(cs.ssim3d(v, x))})
+        plan.close()
+        vox = wk.Z * wk.H * wk.W
+        out.update(metric=METRIC, unit=UNIT, iterations=[r["iters_done"] for r in rows],
+                   value=vox * rows[0]["iters_done"] / (rows[0]["ms_per_solve"] / 1e3),
+                   caps=rows)
     elif name == "cr_sweep_256x256x40":
         # compression-ratio sweep: the same 40-slice volume seen through N shots of
         # R planes each (R = Z / N in {5, 10, 20}), patterns shared by all shots
@@ -557,7 +585,7 @@ def main():
     ap.add_argument("--workload", default=None,
                     help="secondary workload: tikhonov_1024x1024x32, tv_1024x1024x32, "
                          "bm3d_1024x1024x32, tv_128x128x8, batched_64, unrolled_b8, "
-                         "cr_sweep_256x256x40")
+                         "cr_sweep_256x256x40, tol_caps_512x512x16")
     args = ap.parse_args()
     if args.workload:
         run_secondary(args)

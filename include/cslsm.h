@@ -70,8 +70,12 @@ typedef enum {
  *   gamma   >= 0  z-smoothness weight (Sec. III-C); 0 = slice-based model.
  *                 Ignored when Z == 1.
  *   iters   >= 0  maximum number of ADMM iterations.
- *   tol     >= 0  stop once ||v^{k+1}-v^k|| / ||v^k|| < tol (checked every
- *                 check_every iterations; the check synchronises the stream).
+ *   tol     >= 0  stop once ||v^{k+1}-v^k|| / ||v^k|| < tol (Sec. IV-B), checked
+ *                 every check_every iterations ON THE DEVICE: all `iters`
+ *                 iterations are enqueued without any host synchronisation and
+ *                 every kernel after the check that met the tolerance returns
+ *                 at once; the call synchronises `stream` once at its end to
+ *                 report the outcome.
  *                 0 runs exactly `iters` iterations without synchronising.
  *   check_every   >= 1, used only when tol > 0.
  *   denoiser      a cslsm_denoiser.

@@ -45,6 +45,7 @@ struct cslsm_plan_s {
     double *partials = nullptr;  // reduction partials (2 doubles per block)
     int npartials = 0;
     double *red_out = nullptr;  // 2 doubles
+    TolState *tol = nullptr;    // device-side stopping state of tolerance solves
     void *bm3d_ws = nullptr;     // BM3D workspace (zero-filled on allocation)
     size_t bm3d_ws_bytes = 0;
     ZsweepWs zs;                 // persistent z sweep (TV, gamma > 0)
@@ -121,6 +122,7 @@ void free_plan(cslsm_plan_s *p)
     zsweep_release(p->zs);
     cudaFree(p->partials);
     cudaFree(p->red_out);
+    cudaFree(p->tol);
     cudaFree(p->bm3d_ws);
     delete p;
 }
@@ -278,8 +280,14 @@ cslsm_status cslsm_admm_solve(cslsm_plan plan, const float *b, const cslsm_admm_
     }
     if (use_tol) {
         if (!plan->vprev) CSLSM_CUDA(cudaMalloc(&plan->vprev, sizeof(float) * nv));
+        if (!plan->tol) CSLSM_CUDA(cudaMalloc(&plan->tol, sizeof(TolState)));
         CSLSM_CUDA(cudaMemsetAsync(plan->vprev, 0, sizeof(float) * nv, s));
+        CSLSM_CUDA(cudaMemsetAsync(plan->tol, 0, sizeof(TolState), s));
     }
+    // tolerance solves stop on the device: every kernel of the iteration reads
+    // this flag and returns at once after the check that met the tolerance
+    const int *stop = use_tol ? reinterpret_cast<const int *>(plan->tol) : nullptr;  // .stop
+    int checks = 0;
     const bool tv = prm->denoiser == CSLSM_DEN_TV;
     if (tv && prm->lambda > 0.f && prm->tv_inner > tv_max_steps_per_launch()) {
         const size_t need = 4 * (gam > 0.f ? 1 : (size_t)g.Z()) * (size_t)g.HW();
@@ -317,13 +325,14 @@ cslsm_status cslsm_admm_solve(cslsm_plan plan, const float *b, const cslsm_admm_
         double *part = check ? plan->partials : nullptr;
         if (prm->denoiser == CSLSM_DEN_TIKHONOV) {
             st = launch_tikhonov_iter(g, m, store, u, d, b, prm->rho, prm->lambda, gam, vo, vp,
-                                      part, plan->npartials, s);
+                                      part, plan->npartials, s, stop);
             if (st) return st;
         } else if (prm->denoiser == CSLSM_DEN_BM3D) {
             st = launch_xupdate_w(g, m, store, u, d, b, prm->rho, plan->w, vo, vp, part,
-                                  plan->npartials, s);
+                                  plan->npartials, s, stop);
             if (st) return st;
             Bm3dSlices a{};
+            a.stop = stop;
             a.storage = store;
             a.src = plan->w;
             a.u = u;
@@ -350,9 +359,10 @@ cslsm_status cslsm_admm_solve(cslsm_plan plan, const float *b, const cslsm_admm_
             }
         } else {
             st = launch_xupdate_w(g, m, store, u, d, b, prm->rho, plan->w, vo, vp, part,
-                                  plan->npartials, s);
+                                  plan->npartials, s, stop);
             if (st) return st;
             TvSlices a{};
+            a.stop = stop;
             a.storage = store;
             a.w = plan->w;
             a.u = u;
@@ -400,24 +410,26 @@ cslsm_status cslsm_admm_solve(cslsm_plan plan, const float *b, const cslsm_admm_
                                                                  : plan->npartials;
             st = launch_sum_pairs(plan->partials, nblk, plan->red_out, s);
             if (st) return st;
-            double h[2];
-            CSLSM_CUDA(cudaMemcpyAsync(h, plan->red_out, sizeof(h), cudaMemcpyDeviceToHost, s));
-            CSLSM_CUDA(cudaStreamSynchronize(s));
-            rel = h[1] > 0.0 ? std::sqrt(h[0] / h[1]) : INFINITY;
-            if (rel < prm->tol) {
-                stopped = !last;
-                ++k;
-                break;
-            }
+            st = launch_tol_check(plan->red_out, prm->tol, k, plan->tol, s);
+            if (st) return st;
+            ++checks;
         }
     }
     if (used_zsweep) {
         st = zsweep_check(plan->zs, s);
         if (st) return st;
     }
-    if (stopped)  // v^{k} of the final iteration is in vprev
-        CSLSM_CUDA(cudaMemcpyAsync(v_out, plan->vprev, sizeof(float) * nv,
-                                   cudaMemcpyDeviceToDevice, s));
+    if (use_tol && prm->iters > 0) {
+        // a stopped solve's v^{k} is in vprev; then read the outcome (one sync)
+        st = launch_copy_if_stopped(plan->tol, plan->vprev, v_out, nv, s);
+        if (st) return st;
+        TolState h{};
+        CSLSM_CUDA(cudaMemcpyAsync(&h, plan->tol, sizeof(h), cudaMemcpyDeviceToHost, s));
+        CSLSM_CUDA(cudaStreamSynchronize(s));
+        stopped = h.stop != 0;
+        k = stopped ? h.iters_done : prm->iters;
+        rel = checks > 0 ? h.rel : -1.0;
+    }
     if (prm->iters == 0) {  // v^0: nothing computed; report zeros
         CSLSM_CUDA(cudaMemsetAsync(v_out, 0, sizeof(float) * nv, s));
     }

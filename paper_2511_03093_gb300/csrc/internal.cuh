@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 #include <vector>
@@ -74,15 +75,34 @@ cslsm_status launch_adjoint(const Geom &g, Masks m, const float *b, float *v, cu
 // sum (v^{k+1}-vprev)^2 and sum vprev^2 into partials[2*block] and then
 // stores v^{k+1} into vprev.
 // u, d, w have the element type of `storage` (a cslsm_storage value).
+// stop: device flag of a tolerance-stopped solve (the kernel returns at once
+// when it is set), or nullptr; the same for launch_tikhonov_iter.
 cslsm_status launch_xupdate_w(const Geom &g, Masks m, int storage, const void *u, const void *d,
                               const float *b, float rho, void *w, float *v_out, float *vprev,
-                              double *partials, int nblocks_red, cudaStream_t s);
+                              double *partials, int nblocks_red, cudaStream_t s,
+                              const int *stop = nullptr);
 
 // One whole ADMM iteration with the Tikhonov prior fused into one pass:
 // v-update, Gauss-Seidel Tikhonov sweep along z (gamma > 0) and dual update.
 cslsm_status launch_tikhonov_iter(const Geom &g, Masks m, int storage, void *u, void *d,
                                   const float *b, float rho, float lam, float gam, float *v_out,
-                                  float *vprev, double *partials, int nblocks_red, cudaStream_t s);
+                                  float *vprev, double *partials, int nblocks_red, cudaStream_t s,
+                                  const int *stop = nullptr);
+
+// Device-side tolerance stop (Sec. IV-B stopping rule without a host sync per
+// check).  state: {int stop; int iters_done; double rel}.  tol_check: unless
+// already stopped, rel = sqrt(red[0] / red[1]) and, when rel < tol, stop = 1 and
+// iters_done = k + 1.  copy_if_stopped: dst = src when the solve stopped.
+struct TolState {
+    int stop;  // first member: kernels take its address as the stop flag
+    int iters_done;
+    double rel;
+};
+static_assert(offsetof(TolState, stop) == 0, "the stop flag leads TolState");
+cslsm_status launch_tol_check(const double *red, float tol, int k, TolState *state,
+                              cudaStream_t s);
+cslsm_status launch_copy_if_stopped(const TolState *state, const float *src, float *dst,
+                                    size_t n, cudaStream_t s);
 
 // Slice-wise Tikhonov prox out = rho*in/(2 lam + rho).
 cslsm_status launch_tikhonov_prox(const float *in, float *out, long long n, float rho, float lam,
@@ -109,6 +129,7 @@ struct TvSlices {
     float theta;         // TV weight of the prox
     float tau;
     int T;               // Chambolle steps
+    const int *stop = nullptr;  // device flag of a tolerance-stopped solve: skip when set
 };
 // Chambolle TV prox of every listed slice.  Uses the plan-provided dual
 // buffers pbuf (4 * nslices * H * W floats) only when T exceeds the largest
@@ -164,6 +185,7 @@ struct Bm3dSlices {
     void *dual;        // [Z][H][W] receives src - out for those slices, or nullptr
     int Z, H, W, n0, nslices;
     float rho, gamma, sigma;
+    const int *stop = nullptr;  // device flag of a tolerance-stopped solve: skip when set
 };
 int bm3d_nref(int H, int W);
 // Device workspace for nslices slices; it must be zero-filled before its first

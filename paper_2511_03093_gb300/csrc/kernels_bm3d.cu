@@ -69,8 +69,9 @@ template <typename S>
 __global__ void bm3d_prep_kernel(const S *__restrict__ src, const S *__restrict__ u,
                                  int Z, int n0, int ns, int HW, float rho, float gamma,
                                  float inv_rho2g, float *__restrict__ g,
-                                 uint8_t *__restrict__ codes)
+                                 uint8_t *__restrict__ codes, const int *__restrict__ stop)
 {
+    if (stop && *stop) return;  // a tolerance-stopped solve: nothing more to do
     const long long N = (long long)ns * HW;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
          i += (long long)gridDim.x * blockDim.x) {
@@ -149,8 +150,9 @@ __device__ __forceinline__ void scan_column(const uint32_t (*win)[kWinWords], in
 
 __global__ void __launch_bounds__(kMatchWarps * 32)
 bm3d_match_kernel(const uint8_t *__restrict__ codes, int H, int W, int ns, int thr,
-                  int *__restrict__ lists, int *__restrict__ counts)
+                  int *__restrict__ lists, int *__restrict__ counts, const int *__restrict__ stop)
 {
+    if (stop && *stop) return;
     __shared__ uint32_t s_win[kMatchWarps][kWinPx][kWinWords];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     uint32_t (*win)[kWinWords] = s_win[wid];
@@ -320,11 +322,13 @@ struct FilterArgs {
     double *num, *den;    // [ns][H][W] accumulators
     int H, W, ns;
     float sigma;
+    const int *stop;      // tolerance-stopped solve: skip (or nullptr)
 };
 
 template <bool kWiener>
 __global__ void __launch_bounds__(kFilterWarps * 32, 2) bm3d_filter_kernel(const FilterArgs a)
 {
+    if (a.stop && *a.stop) return;
     __shared__ double s_num[kFoot * kFootPitch], s_den[kFoot * kFootPitch];
     __shared__ float s_n[kFoot * kFootPitch];
     __shared__ float s_b[kWiener ? kFoot * kFootPitch : 1];
@@ -451,8 +455,9 @@ template <typename S>
 __global__ void bm3d_finish_kernel(double *__restrict__ num, double *__restrict__ den,
                                    S *__restrict__ out, const S *__restrict__ w,
                                    S *__restrict__ dual, uint8_t *__restrict__ codes,
-                                   long long N)
+                                   long long N, const int *__restrict__ stop)
 {
+    if (stop && *stop) return;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
          i += (long long)gridDim.x * blockDim.x) {
         float v;
@@ -475,8 +480,10 @@ __global__ void bm3d_finish_kernel(double *__restrict__ num, double *__restrict_
 // out = g where no patch fits (the identity), with the same epilogue.
 template <typename S>
 __global__ void bm3d_copy_kernel(const float *__restrict__ g, S *__restrict__ out,
-                                 const S *__restrict__ w, S *__restrict__ dual, long long N)
+                                 const S *__restrict__ w, S *__restrict__ dual, long long N,
+                                 const int *__restrict__ stop)
 {
+    if (stop && *stop) return;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
          i += (long long)gridDim.x * blockDim.x) {
         st<S>(out + i, g[i]);
@@ -560,32 +567,33 @@ Ws carve(void *base, int ns, int H, int W)
 
 template <typename S>
 cslsm_status prep(const S *src, const S *u, int Z, int n0, int ns, int HW, float rho,
-                  float gamma, float *g, uint8_t *codes, cudaStream_t s)
+                  float gamma, float *g, uint8_t *codes, cudaStream_t s,
+                  const int *stop = nullptr)
 {
     LaunchScope ls(K_BM3D_PREP, s);
     bm3d_prep_kernel<S><<<grid_for((long long)ns * HW, 256), 256, 0, s>>>(
-        src, u, Z, n0, ns, HW, rho, gamma, 1.f / (rho + 2.f * gamma), g, codes);
+        src, u, Z, n0, ns, HW, rho, gamma, 1.f / (rho + 2.f * gamma), g, codes, stop);
     CSLSM_LAUNCHED();
     return CSLSM_OK;
 }
 
 cslsm_status match(const uint8_t *codes, int ns, int H, int W, int stage, int *lists,
-                   int *counts, cudaStream_t s)
+                   int *counts, cudaStream_t s, const int *stop = nullptr)
 {
     const long long total = (long long)ns * n_refs(H) * n_refs(W);
     if (total == 0) return CSLSM_OK;
     const int thr = kPS * kPS * (stage == 1 ? kTauHard : kTauWiener);
     LaunchScope ls(K_BM3D_MATCH, s);
     bm3d_match_kernel<<<grid_for(total, kMatchWarps), kMatchWarps * 32, 0, s>>>(
-        codes, H, W, ns, thr, lists, counts);
+        codes, H, W, ns, thr, lists, counts, stop);
     CSLSM_LAUNCHED();
     return CSLSM_OK;
 }
 
 cslsm_status filter(int stage, const float *noisy, const float *guide, const Ws &w, int ns,
-                    int H, int W, float sigma, cudaStream_t s)
+                    int H, int W, float sigma, cudaStream_t s, const int *stop = nullptr)
 {
-    FilterArgs a{noisy, guide, w.lists, w.counts, w.num, w.den, H, W, ns, sigma};
+    FilterArgs a{noisy, guide, w.lists, w.counts, w.num, w.den, H, W, ns, sigma, stop};
     const dim3 grid((n_refs(W) + kRefBlock - 1) / kRefBlock, (n_refs(H) + kRefBlock - 1) / kRefBlock,
                     ns);
     LaunchScope ls(K_BM3D_FILTER, s);
@@ -597,10 +605,11 @@ cslsm_status filter(int stage, const float *noisy, const float *guide, const Ws 
 
 template <typename S>
 cslsm_status finish(double *num, double *den, S *out, const S *w, S *dual, uint8_t *codes,
-                    long long N, cudaStream_t s)
+                    long long N, cudaStream_t s, const int *stop = nullptr)
 {
     LaunchScope ls(K_BM3D_FINISH, s);
-    bm3d_finish_kernel<S><<<grid_for(N, 256), 256, 0, s>>>(num, den, out, w, dual, codes, N);
+    bm3d_finish_kernel<S><<<grid_for(N, 256), 256, 0, s>>>(num, den, out, w, dual, codes, N,
+                                                            stop);
     CSLSM_LAUNCHED();
     return CSLSM_OK;
 }
@@ -617,21 +626,23 @@ cslsm_status slices_typed(const Bm3dSlices &b, void *ws, cudaStream_t s)
     S *dual = b.dual ? (S *)b.dual + (size_t)b.n0 * HW : nullptr;
     const S *src = (const S *)b.src + (size_t)b.n0 * HW;
     cslsm_status e;
+    const int *stop = b.stop;
     if ((e = prep<S>((const S *)b.src, (const S *)b.u, b.Z, b.n0, ns, (int)HW, b.rho, gam, w.g,
-                     w.codes, s)))
+                     w.codes, s, stop)))
         return e;
     if (H < kPS || W < kPS) {  // no patch fits: the denoiser is the identity
         LaunchScope ls(K_BM3D_FINISH, s);
-        bm3d_copy_kernel<S><<<grid_for(N, 256), 256, 0, s>>>(w.g, out, src, dual, N);
+        bm3d_copy_kernel<S><<<grid_for(N, 256), 256, 0, s>>>(w.g, out, src, dual, N, stop);
         CSLSM_LAUNCHED();
         return CSLSM_OK;
     }
-    if ((e = match(w.codes, ns, H, W, 1, w.lists, w.counts, s))) return e;
-    if ((e = filter(1, w.g, nullptr, w, ns, H, W, b.sigma, s))) return e;
-    if ((e = finish<float>(w.num, w.den, w.basic, nullptr, nullptr, w.codes, N, s))) return e;
-    if ((e = match(w.codes, ns, H, W, 2, w.lists, w.counts, s))) return e;
-    if ((e = filter(2, w.g, w.basic, w, ns, H, W, b.sigma, s))) return e;
-    return finish<S>(w.num, w.den, out, src, dual, nullptr, N, s);
+    if ((e = match(w.codes, ns, H, W, 1, w.lists, w.counts, s, stop))) return e;
+    if ((e = filter(1, w.g, nullptr, w, ns, H, W, b.sigma, s, stop))) return e;
+    if ((e = finish<float>(w.num, w.den, w.basic, nullptr, nullptr, w.codes, N, s, stop)))
+        return e;
+    if ((e = match(w.codes, ns, H, W, 2, w.lists, w.counts, s, stop))) return e;
+    if ((e = filter(2, w.g, w.basic, w, ns, H, W, b.sigma, s, stop))) return e;
+    return finish<S>(w.num, w.den, out, src, dual, nullptr, N, s, stop);
 }
 
 }  // namespace

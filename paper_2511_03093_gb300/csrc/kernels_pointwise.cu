@@ -97,8 +97,10 @@ __global__ void __launch_bounds__(kThreads, RMAX >= 32 ? 2 : 4)
 xupdate_w_kernel(const S *__restrict__ u, const S *__restrict__ d,
                  const float *__restrict__ b, const uint32_t *__restrict__ words, int wstride,
                  int HW, int R, float rho, S *__restrict__ w, float *__restrict__ v_out,
-                 float *__restrict__ vprev, double *__restrict__ partials)
+                 float *__restrict__ vprev, double *__restrict__ partials,
+                 const int *__restrict__ stop)
 {
+    if (stop && *stop) return;  // a tolerance-stopped solve: nothing more to do
     const int p = blockIdx.x * kThreads + threadIdx.x;
     const int j = blockIdx.y;
     double sdv = 0.0, sv = 0.0;
@@ -153,8 +155,10 @@ __global__ void __launch_bounds__(kThreads, 2)
 tikhonov_iter_kernel(S *__restrict__ u, S *__restrict__ d, const float *__restrict__ b,
                      const uint32_t *__restrict__ words, int wstride, int HW, int R, int N,
                      float rho, float lam, float gam, float *__restrict__ v_out,
-                     float *__restrict__ vprev, double *__restrict__ partials)
+                     float *__restrict__ vprev, double *__restrict__ partials,
+                     const int *__restrict__ stop)
 {
+    if (stop && *stop) return;
     const int p = blockIdx.x * kThreads + threadIdx.x;
     const int Z = N * R;
     const float den = 2.f * lam + rho + 2.f * gam;
@@ -325,6 +329,31 @@ __global__ void __launch_bounds__(kThreads) psnr_partials_kernel(const float *__
 
 // Sums `nblocks` pairs in a fixed order (one block): out = {sum a, sum c} or,
 // for PSNR, {sum e, max m} -> 10 log10(n V^2 / e).
+// The stopping rule of Sec. IV-B on the device: rel = ||v^{k+1} - v^k|| / ||v^k||
+// from the reduced sums red = {sum (v^{k+1} - v^k)^2, sum (v^k)^2}; below tol the
+// solve stops (every later kernel of the solve returns at once).
+__global__ void tol_check_kernel(const double *__restrict__ red, float tol, int k,
+                                 TolState *__restrict__ state)
+{
+    if (threadIdx.x != 0 || state->stop) return;
+    const double rel = red[1] > 0.0 ? sqrt(red[0] / red[1]) : INFINITY;
+    state->rel = rel;
+    if (rel < (double)tol) {
+        state->stop = 1;
+        state->iters_done = k + 1;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) copy_if_stopped_kernel(
+    const TolState *__restrict__ state, const float *__restrict__ src, float *__restrict__ dst,
+    size_t n)
+{
+    if (!state->stop) return;
+    for (size_t i = blockIdx.x * (size_t)kThreads + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * kThreads)
+        dst[i] = src[i];
+}
+
 template <bool kPsnr>
 __global__ void __launch_bounds__(kThreads) finish_pairs_kernel(const double *__restrict__ partials,
                                                                 int nblocks, size_t n,
@@ -393,14 +422,14 @@ cslsm_status launch_adjoint(const Geom &g, Masks m, const float *b, float *v, cu
 template <typename S>
 cslsm_status xupdate_typed(const Geom &g, Masks m, const void *u_, const void *d_, const float *b,
                            float rho, void *w_, float *v_out, float *vprev, double *partials,
-                           cudaStream_t s)
+                           cudaStream_t s, const int *stop)
 {
     const S *u = (const S *)u_, *d = (const S *)d_;
     S *w = (S *)w_;
     const dim3 grid = pixel_grid(g.HW(), g.N);
 #define XU(RM)                                                                          \
     xupdate_w_kernel<RM, S><<<grid, kThreads, 0, s>>>(u, d, b, m.words, m.wstride, g.HW(), \
-                                                      g.R, rho, w, v_out, vprev, partials)
+                                                      g.R, rho, w, v_out, vprev, partials, stop)
     LaunchScope ls(K_XUPDATE, s);
     if (g.R <= 4) XU(4);
     else if (g.R <= 8) XU(8);
@@ -414,12 +443,12 @@ cslsm_status xupdate_typed(const Geom &g, Masks m, const void *u_, const void *d
 template <typename S>
 cslsm_status tikhonov_typed(const Geom &g, Masks m, void *u_, void *d_, const float *b,
                             float rho, float lam, float gam, float *v_out, float *vprev,
-                            double *partials, cudaStream_t s)
+                            double *partials, cudaStream_t s, const int *stop)
 {
     S *u = (S *)u_, *d = (S *)d_;
     const uintptr_t al = (uintptr_t)u | (uintptr_t)d | (uintptr_t)b | (uintptr_t)m.words |
                          (uintptr_t)v_out;
-    if (!vprev && !partials && g.HW() % 2 == 0 && (al & 7) == 0) {
+    if (!vprev && !partials && !stop && g.HW() % 2 == 0 && (al & 7) == 0) {
         const int pairs = g.HW() / 2;
         const size_t sm = sizeof(float2) * kThreads * (size_t)g.R;
         static_assert(sizeof(float2) * kThreads * CSLSM_MAX_R <= 227 * 1024, "staging too large");
@@ -436,7 +465,7 @@ cslsm_status tikhonov_typed(const Geom &g, Masks m, void *u_, void *d_, const fl
 #define TK(RM)                                                                            \
     tikhonov_iter_kernel<RM, S><<<grid, kThreads, 0, s>>>(u, d, b, m.words, m.wstride,   \
                                                           g.HW(), g.R, g.N, rho, lam, gam, \
-                                                          v_out, vprev, partials)
+                                                          v_out, vprev, partials, stop)
     LaunchScope ls(K_TIK_ITER, s);
     if (g.R <= 4) TK(4);
     else if (g.R <= 8) TK(8);
@@ -449,7 +478,7 @@ cslsm_status tikhonov_typed(const Geom &g, Masks m, void *u_, void *d_, const fl
 
 cslsm_status launch_xupdate_w(const Geom &g, Masks m, int storage, const void *u, const void *d,
                               const float *b, float rho, void *w, float *v_out, float *vprev,
-                              double *partials, int nblocks_red, cudaStream_t s)
+                              double *partials, int nblocks_red, cudaStream_t s, const int *stop)
 {
     const dim3 grid = pixel_grid(g.HW(), g.N);
     if (partials && (int)(grid.x * grid.y) > nblocks_red) {
@@ -458,17 +487,18 @@ cslsm_status launch_xupdate_w(const Geom &g, Masks m, int storage, const void *u
     }
     switch (storage) {
     case CSLSM_STORE_BF16:
-        return xupdate_typed<__nv_bfloat16>(g, m, u, d, b, rho, w, v_out, vprev, partials, s);
+        return xupdate_typed<__nv_bfloat16>(g, m, u, d, b, rho, w, v_out, vprev, partials, s, stop);
     case CSLSM_STORE_FP16:
-        return xupdate_typed<__half>(g, m, u, d, b, rho, w, v_out, vprev, partials, s);
+        return xupdate_typed<__half>(g, m, u, d, b, rho, w, v_out, vprev, partials, s, stop);
     default:
-        return xupdate_typed<float>(g, m, u, d, b, rho, w, v_out, vprev, partials, s);
+        return xupdate_typed<float>(g, m, u, d, b, rho, w, v_out, vprev, partials, s, stop);
     }
 }
 
 cslsm_status launch_tikhonov_iter(const Geom &g, Masks m, int storage, void *u, void *d,
                                   const float *b, float rho, float lam, float gam, float *v_out,
-                                  float *vprev, double *partials, int nblocks_red, cudaStream_t s)
+                                  float *vprev, double *partials, int nblocks_red, cudaStream_t s,
+                                  const int *stop)
 {
     const dim3 grid = pixel_grid(g.HW(), 1);
     if (partials && (int)grid.x > nblocks_red) {
@@ -478,11 +508,13 @@ cslsm_status launch_tikhonov_iter(const Geom &g, Masks m, int storage, void *u, 
     switch (storage) {
     case CSLSM_STORE_BF16:
         return tikhonov_typed<__nv_bfloat16>(g, m, u, d, b, rho, lam, gam, v_out, vprev,
-                                             partials, s);
+                                             partials, s, stop);
     case CSLSM_STORE_FP16:
-        return tikhonov_typed<__half>(g, m, u, d, b, rho, lam, gam, v_out, vprev, partials, s);
+        return tikhonov_typed<__half>(g, m, u, d, b, rho, lam, gam, v_out, vprev, partials, s,
+                                      stop);
     default:
-        return tikhonov_typed<float>(g, m, u, d, b, rho, lam, gam, v_out, vprev, partials, s);
+        return tikhonov_typed<float>(g, m, u, d, b, rho, lam, gam, v_out, vprev, partials, s,
+                                     stop);
     }
 }
 
@@ -512,6 +544,27 @@ cslsm_status launch_psnr_finish(const double *partials, int nblocks, size_t n, d
 {
     LaunchScope ls(K_REDUCE, s);
     finish_pairs_kernel<true><<<1, kThreads, 0, s>>>(partials, nblocks, n, out);
+    CSLSM_LAUNCHED();
+    return CSLSM_OK;
+}
+
+cslsm_status launch_tol_check(const double *red, float tol, int k, TolState *state,
+                              cudaStream_t s)
+{
+    LaunchScope ls(K_REDUCE, s);
+    tol_check_kernel<<<1, 32, 0, s>>>(red, tol, k, state);
+    CSLSM_LAUNCHED();
+    return CSLSM_OK;
+}
+
+cslsm_status launch_copy_if_stopped(const TolState *state, const float *src, float *dst,
+                                    size_t n, cudaStream_t s)
+{
+    long long blocks = ((long long)n + kThreads - 1) / kThreads;
+    if (blocks > 4096) blocks = 4096;
+    if (blocks < 1) blocks = 1;
+    LaunchScope ls(K_REDUCE, s);
+    copy_if_stopped_kernel<<<(unsigned)blocks, kThreads, 0, s>>>(state, src, dst, n);
     CSLSM_LAUNCHED();
     return CSLSM_OK;
 }

@@ -309,6 +309,7 @@ cslsm_status tv_prox_slices(const TvSlices &s, float *pbuf, cudaStream_t st)
     if (e) return e;
     TvLaunch a{};
     a.storage = s.storage;
+    a.stop = s.stop;
     a.w = s.w;
     a.u = s.u;
     a.d = s.d;

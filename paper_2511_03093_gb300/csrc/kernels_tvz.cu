@@ -57,7 +57,8 @@ struct ZsArgs {
     int H, W, Z, T, k, P, hh, TH, TW, RH, tx, ty;
     float rho, gamma, inv_rho2g, theta, inv_theta, tau;
     long long limit_ns;
-    int stall;  // test hook: tile 0 waits in epoch 1 for an id nobody publishes
+    int stall;        // test hook: tile 0 waits in epoch 1 for an id nobody publishes
+    const int *stop;  // device flag of a tolerance-stopped solve (skip when set), or null
 };
 
 __device__ __forceinline__ unsigned long long zs_ns()
@@ -107,6 +108,7 @@ __device__ bool wait_ge(const unsigned *f, unsigned target, int *err, long long 
 template <int B, int RPW, typename S>
 __global__ void __launch_bounds__(B * 32) tvz_sweep_kernel(const ZsArgs a)
 {
+    if (a.stop && *a.stop) return;  // every CTA reads the same flag: all return
     constexpr unsigned FULL = 0xffffffffu;
     constexpr int RH = B * RPW + 2;
     __shared__ Bnd<B> sb;
@@ -467,6 +469,7 @@ cslsm_status launch(const TvSlices &s, const Cfg &f, ZsweepWs &ws, void *u, void
         a.limit_ns = (long long)(g_wait_s * 1e9);
         a.stall = g_stall;
     }
+    a.stop = s.stop;
     a.base = ws.next_base;
     ws.next_base += (unsigned)(a.Z * a.P);
 

@@ -22,6 +22,7 @@ struct TvLaunch {
     float theta, inv_theta, tau;
     int write_final;
     int storage;
+    const int *stop;  // device flag of a tolerance-stopped solve (skip when set), or null
 };
 
 __device__ __forceinline__ float sqrt_approx(float x)
@@ -277,6 +278,7 @@ __device__ __forceinline__ void tv_tile_body(const TvLaunch &a, int bx, int by, 
 template <int C, int B, typename S>
 __global__ void __launch_bounds__(C * B * 32) tv_tile_kernel(const TvLaunch a)
 {
+    if (a.stop && *a.stop) return;
     extern __shared__ float smem[];
     tv_tile_body<C, B, S>(a, blockIdx.x, blockIdx.y, blockIdx.z, smem);
 }
