@@ -520,6 +520,28 @@ def run_secondary(args) -> None:
         out.update(metric="unrolled PnP-ADMM voxel-iterations/s (forward + backward)", unit=UNIT,
                    value=vox * 30 / ((np.mean(fw) + np.mean(bw)) / 1e3), forward_ms=float(np.mean(fw)),
                    backward_ms=float(np.mean(bw)), batch=B, volume=[Z, H, W], iterations=30)
+    elif name == "wnnm_512x512x16":
+        # the WNNM prior (listed in Sec. III-B) on the benchmark volume, z term on
+        wk = synth.WORKLOADS["tvz_512x512x16"]
+        data = synth.generate(wk)
+        plan = cs.Plan(wk.H, wk.W, 1, wk.Z, torch.from_numpy(data["masks"]).to(dev))
+        b = torch.from_numpy(data["b"]).to(dev)
+        v = torch.empty((wk.Z, wk.H, wk.W), dtype=torch.float32, device=dev)
+        iters = 10
+        prm = cs.Params(rho=1.0, lam=0.0, gamma=0.2, iters=iters, denoiser="wnnm",
+                        bm3d_sigma=0.05)
+        cs.timing_read("wnnm_filter", reset=True)
+        cs.timing_enable(1)
+        ms = _timed(lambda: plan.solve(b, prm, v_out=v), max(1, min(args.steps, 3)), 1, flush)
+        cs.timing_enable(0)
+        n_f, ms_f = cs.timing_read("wnnm_filter", reset=True)
+        x = torch.from_numpy(data["x"].astype(np.float32)).to(dev)
+        vox = wk.Z * wk.H * wk.W
+        out.update(metric=METRIC, unit=UNIT, value=vox * iters / (sum(ms) / len(ms) / 1e3),
+                   ms_per_step=sum(ms) / len(ms), iterations=iters,
+                   wnnm_filter_ms_per_launch=ms_f / max(n_f, 1),
+                   psnr_db=float(cs.psnr(v, x)), ssim3d=float(cs.ssim3d(v, x)))
+        plan.close()
     elif name == "tol_caps_512x512x16":
         # the paper's stopping caps (Sec. IV-B): 100 iterations / 1e-3, 200 / 1e-2,
         # checked on the device every iteration, TV + z on the benchmark volume
@@ -585,7 +607,7 @@ def main():
     ap.add_argument("--workload", default=None,
                     help="secondary workload: tikhonov_1024x1024x32, tv_1024x1024x32, "
                          "bm3d_1024x1024x32, tv_128x128x8, batched_64, unrolled_b8, "
-                         "cr_sweep_256x256x40, tol_caps_512x512x16")
+                         "cr_sweep_256x256x40, tol_caps_512x512x16, wnnm_512x512x16")
     args = ap.parse_args()
     if args.workload:
         run_secondary(args)

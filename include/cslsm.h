@@ -51,7 +51,10 @@ typedef enum {
 typedef enum {
     CSLSM_DEN_TIKHONOV = 0, /* psi(u) = ||u||^2, closed form (Sec. III-B, III-C) */
     CSLSM_DEN_TV = 1,       /* isotropic TV, Chambolle dual projection */
-    CSLSM_DEN_BM3D = 2      /* block matching + 3D collaborative filtering */
+    CSLSM_DEN_BM3D = 2,     /* block matching + 3D collaborative filtering */
+    CSLSM_DEN_WNNM = 3      /* weighted nuclear norm minimisation on the BM3D groups
+                               (listed in Sec. III-B; one pass per u-step, noise level
+                               bm3d_sigma) */
 } cslsm_denoiser;
 
 /* Element type of the ADMM state u, d and of the plan's w = v + d workspace

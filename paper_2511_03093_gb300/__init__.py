@@ -20,8 +20,8 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libcslsm.so")
 
-TIKHONOV, TV, BM3D = 0, 1, 2
-DENOISERS = {"tikhonov": TIKHONOV, "tv": TV, "bm3d": BM3D}
+TIKHONOV, TV, BM3D, WNNM = 0, 1, 2, 3
+DENOISERS = {"tikhonov": TIKHONOV, "tv": TV, "bm3d": BM3D, "wnnm": WNNM}
 MAX_R = 32
 STORAGE = {"fp32": 0, "bf16": 1, "fp16": 2}
 STORAGE_DTYPE = {"fp32": torch.float32, "bf16": torch.bfloat16, "fp16": torch.float16}

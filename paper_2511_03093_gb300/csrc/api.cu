@@ -80,14 +80,14 @@ cslsm_status check_params(const cslsm_admm_params *p, bool for_denoise)
     CHECK_ARG(p != nullptr, "params is NULL");
     CHECK_ARG(finite_f(p->rho) && p->rho > 0.f, "rho must be finite and > 0");
     CHECK_ARG(finite_f(p->lambda) && p->lambda >= 0.f, "lambda must be finite and >= 0");
-    CHECK_ARG(p->denoiser >= CSLSM_DEN_TIKHONOV && p->denoiser <= CSLSM_DEN_BM3D,
+    CHECK_ARG(p->denoiser >= CSLSM_DEN_TIKHONOV && p->denoiser <= CSLSM_DEN_WNNM,
               "unknown denoiser %d", p->denoiser);
     if (p->denoiser == CSLSM_DEN_TV) {
         CHECK_ARG(p->tv_inner >= 1, "tv_inner must be >= 1");
         CHECK_ARG(finite_f(p->tv_tau) && p->tv_tau > 0.f && p->tv_tau <= 0.25f,
                   "tv_tau must be in (0, 0.25]");
     }
-    if (p->denoiser == CSLSM_DEN_BM3D)
+    if (p->denoiser == CSLSM_DEN_BM3D || p->denoiser == CSLSM_DEN_WNNM)
         CHECK_ARG(finite_f(p->bm3d_sigma) && p->bm3d_sigma > 0.f, "bm3d_sigma must be > 0");
     if (for_denoise) return CSLSM_OK;
     CHECK_ARG(finite_f(p->gamma) && p->gamma >= 0.f, "gamma must be finite and >= 0");
@@ -300,7 +300,8 @@ cslsm_status cslsm_admm_solve(cslsm_plan plan, const float *b, const cslsm_admm_
             plan->pbuf_floats = need;
         }
     }
-    if (prm->denoiser == CSLSM_DEN_BM3D) {
+    const bool patchwise = prm->denoiser == CSLSM_DEN_BM3D || prm->denoiser == CSLSM_DEN_WNNM;
+    if (patchwise) {
         const size_t need = bm3d_workspace_bytes(gam > 0.f ? 1 : g.Z(), g.H, g.W);
         if (plan->bm3d_ws_bytes < need) {
             CSLSM_CUDA(cudaStreamSynchronize(s));
@@ -327,7 +328,7 @@ cslsm_status cslsm_admm_solve(cslsm_plan plan, const float *b, const cslsm_admm_
             st = launch_tikhonov_iter(g, m, store, u, d, b, prm->rho, prm->lambda, gam, vo, vp,
                                       part, plan->npartials, s, stop);
             if (st) return st;
-        } else if (prm->denoiser == CSLSM_DEN_BM3D) {
+        } else if (patchwise) {
             st = launch_xupdate_w(g, m, store, u, d, b, prm->rho, plan->w, vo, vp, part,
                                   plan->npartials, s, stop);
             if (st) return st;
@@ -347,13 +348,15 @@ cslsm_status cslsm_admm_solve(cslsm_plan plan, const float *b, const cslsm_admm_
             if (gam == 0.f) {
                 a.n0 = 0;
                 a.nslices = g.Z();
-                st = bm3d_slices(a, plan->bm3d_ws, s);
+                st = prm->denoiser == CSLSM_DEN_WNNM ? wnnm_slices(a, plan->bm3d_ws, s)
+                                                     : bm3d_slices(a, plan->bm3d_ws, s);
                 if (st) return st;
             } else {
                 a.nslices = 1;
                 for (int n = 0; n < g.Z(); ++n) {
                     a.n0 = n;
-                    st = bm3d_slices(a, plan->bm3d_ws, s);
+                    st = prm->denoiser == CSLSM_DEN_WNNM ? wnnm_slices(a, plan->bm3d_ws, s)
+                                                         : bm3d_slices(a, plan->bm3d_ws, s);
                     if (st) return st;
                 }
             }
@@ -458,7 +461,7 @@ cslsm_status cslsm_denoise(int denoiser, const float *in, float *out, int Z, int
     cudaStream_t s = as_stream(stream);
     if (denoiser == CSLSM_DEN_TIKHONOV)
         return launch_tikhonov_prox(in, out, (long long)nv, prm->rho, prm->lambda, s);
-    if (denoiser == CSLSM_DEN_BM3D) {
+    if (denoiser == CSLSM_DEN_BM3D || denoiser == CSLSM_DEN_WNNM) {
         const size_t need = bm3d_workspace_bytes(Z, H, W);
         void *ws = nullptr;
         CSLSM_CUDA(cudaMallocAsync(&ws, need, s));
@@ -482,7 +485,7 @@ cslsm_status cslsm_denoise(int denoiser, const float *in, float *out, int Z, int
         a.rho = 1.f;
         a.gamma = 0.f;
         a.sigma = prm->bm3d_sigma;
-        st = bm3d_slices(a, ws, s);
+        st = denoiser == CSLSM_DEN_WNNM ? wnnm_slices(a, ws, s) : bm3d_slices(a, ws, s);
         cudaFreeAsync(ws, s);
         return st;
     }

@@ -32,7 +32,7 @@ void set_error(const char *fmt, ...);
 enum KernelId {
     K_PACK = 0, K_FORWARD, K_ADJOINT, K_XUPDATE, K_TIK_ITER, K_TIK_PROX, K_TV_TILE, K_PSNR,
     K_REDUCE, K_BM3D_PREP, K_BM3D_MATCH, K_BM3D_FILTER, K_BM3D_FINISH, K_BATCH, K_DIFF, K_TVZ,
-    K_SSIM, K_COUNT
+    K_SSIM, K_WNNM, K_COUNT
 };
 
 // Wrap every kernel launch: counts it and, when timing is on, records CUDA
@@ -192,6 +192,8 @@ int bm3d_nref(int H, int W);
 // use (the accumulators are cleared again by every call).
 size_t bm3d_workspace_bytes(int nslices, int H, int W);
 cslsm_status bm3d_slices(const Bm3dSlices &b, void *ws, cudaStream_t s);
+// WNNM u-step on the same groups and workspace (hard-stage matching, one pass).
+cslsm_status wnnm_slices(const Bm3dSlices &b, void *ws, cudaStream_t s);
 cslsm_status bm3d_stage_only(int stage, const float *noisy, const float *guide, float *out,
                              int nslices, int H, int W, float sigma, void *ws, cudaStream_t s);
 cslsm_status bm3d_match_only(const float *img, int nslices, int H, int W, int stage, int *lists,

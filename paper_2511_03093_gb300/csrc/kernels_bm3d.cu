@@ -448,6 +448,189 @@ __global__ void __launch_bounds__(kFilterWarps * 32, 2) bm3d_filter_kernel(const
     }
 }
 
+// ---- WNNM (weighted nuclear norm minimisation) on the same groups ------------
+//
+// One warp per group of m <= 16 patches from the hard-stage block matching: lane
+// pair (k, h) holds rows 4h..4h+3 of patch k, i.e. half of column k of the
+// 64 x m group matrix Y.  The columns are centred on the mean patch, then
+// orthogonalised by one-sided (Hestenes) Jacobi rotations: 15 rounds of 8
+// disjoint column pairs per sweep (round-robin pairing), a fixed number of
+// sweeps, the same (c, s) computed bit for bit by both members of a pair.
+// The rotated columns are B = Yc V with norms s_k (the singular values), so the
+// estimate is Xc = B diag(x_k / s_k) V^T with the weighted soft threshold
+// x_k = max(s_k - sigma^2 w_k, 0), w_k = c sqrt(m) / (sigma_hat_k + eps),
+// sigma_hat_k = sqrt(max(s_k^2 - 64 sigma^2, 0)); Xhat = Xc + mean.  Every
+// estimated patch is aggregated with weight 1 (FP64 sums; the counts are exact).
+constexpr int kJacobiSweeps = 8;
+constexpr float kWnnmC = 2.8284271247461903f;  // 2 sqrt(2)
+
+struct WnnmArgs {
+    const float *noisy;  // [ns][H][W] g
+    const int *lists;    // [ns][nref][16]
+    const int *counts;   // [ns][nref]
+    double *num, *den;   // [ns][H][W] accumulators
+    int H, W, ns;
+    float sigma;
+    const int *stop;
+};
+
+// Partner of column k in round r of the round robin over 16 columns.
+__device__ __forceinline__ int rr_partner(int k, int r)
+{
+    if (k == 0) return r != 0 ? r : 15;
+    int q = (2 * r - k) % 15;
+    if (q < 0) q += 15;
+    if (q == 0) q = 15;
+    return q == k ? 0 : q;
+}
+
+__global__ void __launch_bounds__(kFilterWarps * 32, 2) wnnm_filter_kernel(const WnnmArgs a)
+{
+    if (a.stop && *a.stop) return;
+    constexpr unsigned FULL = 0xffffffffu;
+    __shared__ double s_num[kFoot * kFootPitch], s_den[kFoot * kFootPitch];
+    __shared__ float s_n[kFoot * kFootPitch];
+    __shared__ float s_mu[kFilterWarps][kPS * kPS];
+    __shared__ float s_v[kFilterWarps][kMaxGroup][kMaxGroup + 1];  // [row l][column k]
+    __shared__ float s_f[kFilterWarps][kMaxGroup];
+    const int H = a.H, W = a.W;
+    const int nri = n_refs(H), nrj = n_refs(W);
+    const int sl = blockIdx.z;
+    const int bi = blockIdx.y * kRefBlock, bj = blockIdx.x * kRefBlock;
+    const int ei = min(bi + kRefBlock, nri) - 1, ej = min(bj + kRefBlock, nrj) - 1;
+    const int f0 = max(0, ref_pos(bi, H) - kHalfWin), f1 = min(H, ref_pos(ei, H) + kHalfWin + kPS);
+    const int g0 = max(0, ref_pos(bj, W) - kHalfWin), g1 = min(W, ref_pos(ej, W) + kHalfWin + kPS);
+    const int fh = f1 - f0, fw = g1 - g0;
+    const size_t HW = (size_t)H * W;
+    const float *noisy = a.noisy + sl * HW;
+    for (int idx = threadIdx.x; idx < fh * fw; idx += blockDim.x) {
+        const int y = idx / fw, x = idx - y * fw;
+        const int l = y * kFootPitch + x;
+        s_num[l] = 0.0;
+        s_den[l] = 0.0;
+        s_n[l] = noisy[(size_t)(f0 + y) * W + g0 + x];
+    }
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int k = lane >> 1, h = lane & 1;
+    const float sigma = a.sigma, s2 = sigma * sigma;
+    const int nblk = (ei - bi + 1) * (ej - bj + 1);
+    for (int rr = wid; rr < nblk; rr += kFilterWarps) {
+        const int r = (bi + rr / (ej - bj + 1)) * nrj + bj + rr % (ej - bj + 1);
+        const size_t gi = (size_t)sl * nri * nrj + r;
+        const int m = a.counts[gi];
+        const bool act = k < m;
+        const int lin = act ? a.lists[gi * kMaxGroup + k] : a.lists[gi * kMaxGroup];
+        const int py = lin / W - f0, px = lin % W - g0;
+        float x[4 * kPS];  // [rw * 8 + c]: pixel (py + 4h + rw, px + c)
+#pragma unroll
+        for (int rw = 0; rw < 4; ++rw)
+#pragma unroll
+            for (int c = 0; c < kPS; ++c)
+                x[rw * kPS + c] = act ? s_n[(py + 4 * h + rw) * kFootPitch + px + c] : 0.f;
+        // the mean patch over the m active columns (butterfly over lanes of this half)
+        const float inv_m = 1.f / (float)m;
+#pragma unroll
+        for (int i = 0; i < 4 * kPS; ++i) {
+            float t = x[i];
+            t += __shfl_xor_sync(FULL, t, 2);
+            t += __shfl_xor_sync(FULL, t, 4);
+            t += __shfl_xor_sync(FULL, t, 8);
+            t += __shfl_xor_sync(FULL, t, 16);
+            const float mu = t * inv_m;
+            if (k == 0) s_mu[wid][h * 4 * kPS + i] = mu;
+            x[i] = act ? x[i] - mu : 0.f;
+        }
+        // V = I: lane (k, h) holds V[8h + j][k]
+        float vc[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) vc[j] = (8 * h + j == k) ? 1.f : 0.f;
+        for (int sw = 0; sw < kJacobiSweeps; ++sw) {
+            for (int rd = 0; rd < 15; ++rd) {
+                const int p = rr_partner(k, rd);
+                const int src = 2 * p + h;
+                float own2 = 0.f, dot = 0.f;
+#pragma unroll
+                for (int i = 0; i < 4 * kPS; ++i) {
+                    const float o = __shfl_sync(FULL, x[i], src);
+                    own2 = fmaf(x[i], x[i], own2);
+                    dot = fmaf(x[i], o, dot);
+                }
+                own2 += __shfl_xor_sync(FULL, own2, 1);
+                dot += __shfl_xor_sync(FULL, dot, 1);
+                const float oth2 = __shfl_sync(FULL, own2, src);
+                const bool lo = k < p;
+                const float alpha = lo ? own2 : oth2, beta = lo ? oth2 : own2;
+                float c = 1.f, sn = 0.f;
+                if (fabsf(dot) > 1e-7f * sqrtf(alpha * beta)) {
+                    const float zeta = (beta - alpha) / (2.f * dot);
+                    const float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+                    c = 1.f / sqrtf(1.f + t * t);
+                    sn = c * t;
+                }
+#pragma unroll
+                for (int i = 0; i < 4 * kPS; ++i) {
+                    const float o = __shfl_sync(FULL, x[i], src);
+                    x[i] = lo ? c * x[i] - sn * o : sn * o + c * x[i];
+                }
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const float o = __shfl_sync(FULL, vc[j], src);
+                    vc[j] = lo ? c * vc[j] - sn * o : sn * o + c * vc[j];
+                }
+            }
+        }
+        // singular values and the weighted soft threshold
+        float nrm2 = 0.f;
+#pragma unroll
+        for (int i = 0; i < 4 * kPS; ++i) nrm2 = fmaf(x[i], x[i], nrm2);
+        nrm2 += __shfl_xor_sync(FULL, nrm2, 1);
+        const float sk = sqrtf(nrm2);
+        const float sh = sqrtf(fmaxf(nrm2 - 64.f * s2, 0.f));
+        const float wk = kWnnmC * sqrtf((float)m) / (sh + 1e-8f);
+        const float xk = fmaxf(sk - s2 * wk, 0.f);
+        if (h == 0) s_f[wid][k] = (act && sk > 0.f) ? xk / sk : 0.f;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) s_v[wid][8 * h + j][k] = vc[j];
+        __syncwarp();
+        // column k of Xc = sum_kk B[:, kk] f_kk V[k][kk]
+        float o[4 * kPS];
+#pragma unroll
+        for (int i = 0; i < 4 * kPS; ++i) o[i] = 0.f;
+        for (int kk = 0; kk < kMaxGroup; ++kk) {
+            const float coef = s_f[wid][kk] * s_v[wid][k][kk];
+#pragma unroll
+            for (int i = 0; i < 4 * kPS; ++i)
+                o[i] = fmaf(coef, __shfl_sync(FULL, x[i], 2 * kk + h), o[i]);
+        }
+        if (act) {
+#pragma unroll
+            for (int rw = 0; rw < 4; ++rw)
+#pragma unroll
+                for (int c = 0; c < kPS; ++c) {
+                    const int l = (py + 4 * h + rw) * kFootPitch + px + c;
+                    const float est = o[rw * kPS + c] + s_mu[wid][h * 4 * kPS + rw * kPS + c];
+                    atomicAdd(&s_num[l], (double)est);
+                    atomicAdd(&s_den[l], 1.0);
+                }
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    double *num = a.num + sl * HW, *den = a.den + sl * HW;
+    for (int idx = threadIdx.x; idx < fh * fw; idx += blockDim.x) {
+        const int y = idx / fw, x = idx - y * fw;
+        const int l = y * kFootPitch + x;
+        const double d = s_den[l];
+        if (d != 0.0) {
+            const size_t o = (size_t)(f0 + y) * W + g0 + x;
+            atomicAdd(&num[o], s_num[l]);
+            atomicAdd(&den[o], d);
+        }
+    }
+}
+
 // out = num / den (or out = num when den is null) and clears the
 // accumulators; optionally dual = w - out (the ADMM dual update of the
 // slices) and the 8-bit codes of out for the next stage's matching.
@@ -614,6 +797,45 @@ cslsm_status finish(double *num, double *den, S *out, const S *w, S *dual, uint8
     return CSLSM_OK;
 }
 
+cslsm_status wnnm_filter(const float *noisy, const Ws &w, int ns, int H, int W, float sigma,
+                         cudaStream_t s, const int *stop)
+{
+    WnnmArgs a{noisy, w.lists, w.counts, w.num, w.den, H, W, ns, sigma, stop};
+    const dim3 grid((n_refs(W) + kRefBlock - 1) / kRefBlock, (n_refs(H) + kRefBlock - 1) / kRefBlock,
+                    ns);
+    LaunchScope ls(K_WNNM, s);
+    wnnm_filter_kernel<<<grid, kFilterWarps * 32, 0, s>>>(a);
+    CSLSM_LAUNCHED();
+    return CSLSM_OK;
+}
+
+template <typename S>
+cslsm_status wnnm_typed(const Bm3dSlices &b, void *ws, cudaStream_t s)
+{
+    const int H = b.H, W = b.W, ns = b.nslices;
+    const size_t HW = (size_t)H * W;
+    const long long N = (long long)ns * HW;
+    const Ws w = carve(ws, ns, H, W);
+    const float gam = b.Z > 1 ? b.gamma : 0.f;
+    S *out = (S *)b.out + (size_t)b.n0 * HW;
+    S *dual = b.dual ? (S *)b.dual + (size_t)b.n0 * HW : nullptr;
+    const S *src = (const S *)b.src + (size_t)b.n0 * HW;
+    const int *stop = b.stop;
+    cslsm_status e;
+    if ((e = prep<S>((const S *)b.src, (const S *)b.u, b.Z, b.n0, ns, (int)HW, b.rho, gam, w.g,
+                     w.codes, s, stop)))
+        return e;
+    if (H < kPS || W < kPS) {  // no patch fits: the denoiser is the identity
+        LaunchScope ls(K_BM3D_FINISH, s);
+        bm3d_copy_kernel<S><<<grid_for(N, 256), 256, 0, s>>>(w.g, out, src, dual, N, stop);
+        CSLSM_LAUNCHED();
+        return CSLSM_OK;
+    }
+    if ((e = match(w.codes, ns, H, W, 1, w.lists, w.counts, s, stop))) return e;
+    if ((e = wnnm_filter(w.g, w, ns, H, W, b.sigma, s, stop))) return e;
+    return finish<S>(w.num, w.den, out, src, dual, nullptr, N, s, stop);
+}
+
 template <typename S>
 cslsm_status slices_typed(const Bm3dSlices &b, void *ws, cudaStream_t s)
 {
@@ -654,6 +876,15 @@ size_t bm3d_workspace_bytes(int ns, int H, int W)
     const size_t HW = (size_t)H * W, nref = (size_t)n_refs(H) * n_refs(W);
     return 2 * al(ns * HW * sizeof(float)) + 2 * al(ns * HW * sizeof(double)) + al(ns * HW) +
            al(ns * nref * kMaxGroup * sizeof(int)) + al(ns * nref * sizeof(int)) + 256;
+}
+
+cslsm_status wnnm_slices(const Bm3dSlices &b, void *ws, cudaStream_t s)
+{
+    cslsm_status e = upload_constants();
+    if (e) return e;
+    if (b.storage == CSLSM_STORE_BF16) return wnnm_typed<__nv_bfloat16>(b, ws, s);
+    if (b.storage == CSLSM_STORE_FP16) return wnnm_typed<__half>(b, ws, s);
+    return wnnm_typed<float>(b, ws, s);
 }
 
 cslsm_status bm3d_slices(const Bm3dSlices &b, void *ws, cudaStream_t s)

@@ -20,7 +20,7 @@ const char *const kNames[K_COUNT] = {"pack_masks", "forward",  "adjoint",      "
                                      "tikhonov_iter", "tikhonov_prox", "tv_tile",
                                      "psnr_partials", "reduce_finish", "bm3d_prep",
                                      "bm3d_match", "bm3d_filter", "bm3d_finish",
-                                     "batch_persistent", "unrolled", "tvz_sweep", "ssim3d"};
+                                     "batch_persistent", "unrolled", "tvz_sweep", "ssim3d", "wnnm_filter"};
 
 struct Rec {
     int kernel;
