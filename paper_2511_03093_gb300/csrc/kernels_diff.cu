@@ -42,6 +42,26 @@ namespace cslsm {
 namespace {
 
 constexpr int kT = 256;
+// The three scalar gradients are accumulated in kAccCopies FP64 copies each
+// (one atomic per block into copy blockIdx % kAccCopies), summed at the end:
+// one address per scalar would serialise tens of thousands of atomics a launch.
+constexpr int kAccCopies = 64;
+
+// Adds the block's sum of v to acc[idx][blockIdx.x % kAccCopies].  Every thread
+// of the block must call it.
+__device__ __forceinline__ void block_acc(double v, double *acc, int idx)
+{
+    __shared__ double s_part[kT / 32];
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kT / 32; ++w) t += s_part[w];
+        atomicAdd(acc + idx * kAccCopies + blockIdx.x % kAccCopies, t);
+    }
+    __syncthreads();
+}
 
 struct Geo {
     int B, Z, H, W;
@@ -128,8 +148,7 @@ __global__ void ux_bwd_kernel(const float *__restrict__ U, const float *__restri
             lbar[o] += mbar * m * (1.f - m);
         }
     }
-    for (int off = 16; off > 0; off >>= 1) rho_bar += __shfl_down_sync(0xffffffffu, rho_bar, off);
-    if ((threadIdx.x & 31) == 0) atomicAdd(acc, rho_bar);
+    block_acc(rho_bar, acc, 0);
 }
 
 // ---- u-step: g formation -----------------------------------------------------
@@ -170,14 +189,8 @@ __global__ void hform_bwd_kernel(const float *__restrict__ Hbar, const float *__
         }
         rb = (double)(hb * (Wn[o] - h) / den);
     }
-    for (int off = 16; off > 0; off >>= 1) {
-        rb += __shfl_down_sync(0xffffffffu, rb, off);
-        gb += __shfl_down_sync(0xffffffffu, gb, off);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        atomicAdd(acc + 0, rb);
-        atomicAdd(acc + 1, gb);
-    }
+    block_acc(rb, acc, 0);
+    block_acc(gb, acc, 1);
 }
 
 // ---- Huber-TV prox: dual projected gradient ----------------------------------
@@ -263,8 +276,7 @@ __global__ void prox_out_bwd_kernel(const float *__restrict__ P, Geo g, float th
         b1[p] = i < g.H - 1 ? theta * (ub[p + g.W] - uc) : 0.f;
         b2[p] = j < g.W - 1 ? theta * (ub[p + 1] - uc) : 0.f;
     }
-    for (int off = 16; off > 0; off >>= 1) tb += __shfl_down_sync(0xffffffffu, tb, off);
-    if ((threadIdx.x & 31) == 0) atomicAdd(acc + 2, tb);
+    block_acc(tb, acc, 2);
 }
 
 // Reverse of one dual step, part 1: abar = J_proj(a)^T pbar^{t+1}; the kappa
@@ -298,8 +310,7 @@ __global__ void dual_bwd_a_kernel(const DualArgs A, const float *__restrict__ Pb
         const float theta = 1.f / A.inv_theta;
         tb = (double)(kbar * (-eps / (theta * theta)));
     }
-    for (int off = 16; off > 0; off >>= 1) tb += __shfl_down_sync(0xffffffffu, tb, off);
-    if ((threadIdx.x & 31) == 0) atomicAdd(acc + 2, tb);
+    block_acc(tb, acc, 2);
 }
 
 // qbar = tau * grad^T abar = -tau div abar (a depends on q through tau grad q).
@@ -334,8 +345,7 @@ __global__ void dual_bwd_b_kernel(const DualArgs A, const float *__restrict__ Ab
         Hbar[bi * g.HW() + p] -= qc * A.inv_theta;
         tb = (double)(qc * hv * A.inv_theta * A.inv_theta);
     }
-    for (int off = 16; off > 0; off >>= 1) tb += __shfl_down_sync(0xffffffffu, tb, off);
-    if ((threadIdx.x & 31) == 0) atomicAdd(acc + 2, tb);
+    block_acc(tb, acc, 2);
 }
 
 // lbar -> dL/dlogits already includes m (1 - m); Uold_bar etc. are plain adds.
@@ -359,7 +369,8 @@ size_t ws_bytes(const Geo &g, int T, int S)
 {
     const size_t nv = (size_t)g.B * g.NV() * 4, hw = (size_t)g.B * g.HW() * 4;
     return al(nv) * 3 + al(hw) + 2 * al(2 * hw) + al((size_t)(T + 1) * 2 * hw) +
-           2 * al((size_t)(S + 1) * nv) + al(nv) * 4 + al(hw) + 3 * al(2 * hw) + al(64);
+           2 * al((size_t)(S + 1) * nv) + al(nv) * 4 + al(hw) + 3 * al(2 * hw) +
+           al(3 * kAccCopies * sizeof(double));
 }
 
 Ws carve(void *base, const Geo &g, int T, int S)
@@ -389,7 +400,7 @@ Ws carve(void *base, const Geo &g, int T, int S)
     w.Pbar_a = take(2 * hw);
     w.Pbar_b = take(2 * hw);
     w.Abar = take(2 * hw);
-    w.acc = (double *)take(64);
+    w.acc = (double *)take(3 * kAccCopies * sizeof(double));
     return w;
 }
 
@@ -501,7 +512,7 @@ cslsm_status unrolled_backward(int B, int Z, int H, int W, float rho, float lam,
     Ws w = carve(ws, g, T, S);
     const size_t nv = (size_t)B * g.NV(), HW = g.HW(), hw2 = (size_t)B * 2 * HW;
     const float den = rho + 2.f * gz, theta = lam / den;
-    CSLSM_CUDA(cudaMemsetAsync(w.acc, 0, 3 * sizeof(double), s));
+    CSLSM_CUDA(cudaMemsetAsync(w.acc, 0, 3 * kAccCopies * sizeof(double), s));
     CSLSM_CUDA(cudaMemsetAsync(logits_bar, 0, nv * 4, s));
     // adjoint of the state after the last iteration: only v^K is observed
     CSLSM_CUDA(cudaMemsetAsync(w.Ubar_new, 0, nv * 4, s));
@@ -572,9 +583,11 @@ cslsm_status unrolled_backward(int B, int Z, int H, int W, float rho, float lam,
         }
     }
     // scalars: rho_direct, gamma_direct, theta_total -> (rho, lambda, gamma)
-    double acc[3];
-    CSLSM_CUDA(cudaMemcpyAsync(acc, w.acc, sizeof(acc), cudaMemcpyDeviceToHost, s));
+    double copies[3 * kAccCopies], acc[3] = {0.0, 0.0, 0.0};
+    CSLSM_CUDA(cudaMemcpyAsync(copies, w.acc, sizeof(copies), cudaMemcpyDeviceToHost, s));
     CSLSM_CUDA(cudaStreamSynchronize(s));
+    for (int q = 0; q < 3; ++q)
+        for (int c = 0; c < kAccCopies; ++c) acc[q] += copies[q * kAccCopies + c];
     const double dd = (double)den;
     double out[3];
     out[1] = acc[2] / dd;                                   // dtheta/dlambda = 1/den
