@@ -281,10 +281,9 @@ cslsm_status cslsm_unrolled_backward(const float *logits, const float *b, int B,
 
 /* ---- allocation-free BM3D ------------------------------------------------
  * The paper has no counterpart to this entry point; it serves callers that
- * cannot allocate device memory when they denoise (inside a CUDA graph
- * capture that forbids allocation, under a fixed memory budget owned by the
- * host application, or in a loop where an allocation's latency or failure is
- * not acceptable).
+ * cannot allocate device memory when they denoise (under a fixed memory
+ * budget owned by the host application, or in a loop where an allocation's
+ * latency or failure is not acceptable).
  *
  * cslsm_denoise_bm3d_noalloc computes exactly what cslsm_denoise does with
  * the BM3D prior at noise level sigma (in, out: device [Z][H][W], not
@@ -296,11 +295,10 @@ cslsm_status cslsm_unrolled_backward(const float *logits, const float *b, int B,
  * voxel, e.g. 8.5 MB for one 512 x 512 slice) exceeds it returns
  * CSLSM_ERR_INVALID_ARG before any GPU work.
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture.  Every call on a device shares the one array and clears
- * the part it uses at its start, so calls whose GPU work overlaps (on
- * different streams, or from different host threads) race and give wrong
- * results; serialise them on one stream. */
+ * (cudaGetSymbolAddress) with that device current.  Every call on a device
+ * shares the one array and clears the part it uses at its start, so calls
+ * whose GPU work overlaps (on different streams, or from different host
+ * threads) race and give wrong results; serialise them on one stream. */
 size_t cslsm_bm3d_noalloc_capacity(void);
 size_t cslsm_bm3d_scratch_bytes(int Z, int H, int W);
 cslsm_status cslsm_denoise_bm3d_noalloc(const float *in, float *out, int Z, int H, int W,

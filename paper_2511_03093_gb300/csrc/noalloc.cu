@@ -1,7 +1,6 @@
 // Allocation-free BM3D denoiser entry point.
 //
-// Some callers cannot allocate device memory at the moment they denoise: code
-// running while a CUDA graph is being captured with allocation forbidden, a
+// Some callers cannot allocate device memory at the moment they denoise: a
 // host application that owns a fixed memory budget and forbids libraries from
 // growing it, or a real-time loop where an allocation's latency or failure is
 // not acceptable.  cslsm_denoise with BM3D takes its scratch (the basic
@@ -26,7 +25,7 @@ namespace {
 
 constexpr size_t kScratchBytes = 64ull << 20;  // 64 MiB
 
-__device__ __align__(256) unsigned char g_bm3d_scratch[kScratchBytes];
+static __device__ __align__(256) unsigned char g_bm3d_scratch[kScratchBytes];
 
 std::mutex g_mu;
 std::vector<void *> g_scratch_addr;  // per device, filled at first use
