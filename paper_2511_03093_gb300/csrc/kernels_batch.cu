@@ -242,12 +242,14 @@ __device__ void tv_unit(const BItem &it, const BDesc &D, int n, int j, int tile,
     }
     __syncthreads();
     const int ns = min(D.k, D.T - j * D.k);
+    // rows exact after the phase: the own tile, and the row above it for u_n
+    const int lo = hh - (j == D.P - 1 ? 1 : 0), hi = hh + TH;
     if (interior)
         sweep_steps<true, B, RPW>(sb, p1, p2, g, gdn, mr, mc0, mc1, inv_theta, D.tau, ns, wp,
-                                  lane);
+                                  lane, lo, hi);
     else
         sweep_steps<false, B, RPW>(sb, p1, p2, g, gdn, mr, mc0, mc1, inv_theta, D.tau, ns, wp,
-                                   lane);
+                                   lane, lo, hi);
     if (j < D.P - 1) {  // p of the own tile for the next phase
         float *Q1 = it.pbuf + ((size_t)(j & 1) * 2 * Zp + slot) * HW;
         float *Q2 = Q1 + (size_t)Zp * HW;

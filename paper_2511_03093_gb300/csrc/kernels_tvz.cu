@@ -285,12 +285,16 @@ __global__ void __launch_bounds__(B * 32) tvz_sweep_kernel(const ZsArgs a)
             }
             __syncthreads();
             const int ns = min(a.k, a.T - j * a.k);
+            // rows that must be exact after the phase: the own tile (published, or
+            // kept for the next phase), plus the row above it when u_n = g - theta
+            // div p is formed at the slice end
+            const int lo = hh - (j == a.P - 1 ? 1 : 0), hi = hh + TH;
             if (interior)
                 sweep_steps<true, B, RPW>(sb, p1, p2, g, gdn, mr, mc0, mc1, inv_theta, tau, ns,
-                                          wp, lane);
+                                          wp, lane, lo, hi);
             else
                 sweep_steps<false, B, RPW>(sb, p1, p2, g, gdn, mr, mc0, mc1, inv_theta, tau, ns,
-                                           wp, lane);
+                                           wp, lane, lo, hi);
             if (j < a.P - 1) {  // publish p of the own tile
                 float *Q1 = a.pbuf + (size_t)(e & 1) * 2 * HW, *Q2 = Q1 + HW;
 #pragma unroll

@@ -50,17 +50,75 @@ struct Region {
     __host__ __device__ static size_t array_floats(int RH) { return (size_t)PW * RH + 4; }
 };
 
+// Packed pairs of FP32 operations (PTX .f32x2): each half is computed and
+// rounded to nearest even exactly as the scalar instruction would, so the
+// pair forms below give the same bits as two scalar operations in half the
+// instructions.
+__device__ __forceinline__ unsigned long long f2_pack(float2 v)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(v.x), "f"(v.y));
+    return r;
+}
+
+__device__ __forceinline__ float2 f2_unpack(unsigned long long r)
+{
+    float2 v;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+    return v;
+}
+
+__device__ __forceinline__ float2 add2(float2 a, float2 b)
+{
+    unsigned long long r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2_pack(a)), "l"(f2_pack(b)));
+    return f2_unpack(r);
+}
+
+__device__ __forceinline__ float2 sub2(float2 a, float2 b)
+{
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2_pack(a)), "l"(f2_pack(b)));
+    return f2_unpack(r);
+}
+
+__device__ __forceinline__ float2 mul2(float2 a, float2 b)
+{
+    unsigned long long r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2_pack(a)), "l"(f2_pack(b)));
+    return f2_unpack(r);
+}
+
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c)
+{
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(f2_pack(a)), "l"(f2_pack(b)), "l"(f2_pack(c)));
+    return f2_unpack(r);
+}
+
+// Shared tail of one Chambolle update of a lane's two columns from the
+// gradients (gx, gy) of q: |grad q| per column, then
+// p <- (p + tau grad q) / (1 + tau |grad q|) for both components.
+__device__ __forceinline__ float2 chambolle_tail(float2 gx, float2 gy, float2 pc, float tau,
+                                                 float2 &p2c)
+{
+    const float2 s = fma2(gx, gx, mul2(gy, gy));
+    const float2 t2 = make_float2(tau, tau);
+    const float2 den = fma2(t2, make_float2(sqrt_approx(s.x), sqrt_approx(s.y)),
+                            make_float2(1.f, 1.f));
+    const float2 inv = make_float2(rcp_approx(den.x), rcp_approx(den.y));
+    p2c = mul2(fma2(t2, gy, p2c), inv);
+    return mul2(fma2(t2, gx, pc), inv);
+}
+
 // One Chambolle update of the two columns a lane owns at row i.
 __device__ __forceinline__ float2 chambolle_pair(float2 qc, float2 qn, float qr, float2 pc,
                                                  float mr, float mc0, float mc1, float tau,
                                                  float2 &p2c)
 {
-    const float gx0 = (qn.x - qc.x) * mr, gy0 = (qc.y - qc.x) * mc0;
-    const float gx1 = (qn.y - qc.y) * mr, gy1 = (qr - qc.y) * mc1;
-    const float i0 = rcp_approx(fmaf(tau, sqrt_approx(fmaf(gx0, gx0, gy0 * gy0)), 1.f));
-    const float i1 = rcp_approx(fmaf(tau, sqrt_approx(fmaf(gx1, gx1, gy1 * gy1)), 1.f));
-    p2c = make_float2(fmaf(tau, gy0, p2c.x) * i0, fmaf(tau, gy1, p2c.y) * i1);
-    return make_float2(fmaf(tau, gx0, pc.x) * i0, fmaf(tau, gx1, pc.y) * i1);
+    const float2 gx = mul2(sub2(qn, qc), make_float2(mr, mr));
+    const float2 gy = mul2(sub2(make_float2(qc.y, qr), qc), make_float2(mc0, mc1));
+    return chambolle_tail(gx, gy, pc, tau, p2c);
 }
 
 // chambolle_pair with every mask equal to one (a tile whose region lies inside
@@ -68,12 +126,17 @@ __device__ __forceinline__ float2 chambolle_pair(float2 qc, float2 qn, float qr,
 __device__ __forceinline__ float2 chambolle_pair_interior(float2 qc, float2 qn, float qr,
                                                           float2 pc, float tau, float2 &p2c)
 {
-    const float gx0 = qn.x - qc.x, gy0 = qc.y - qc.x;
-    const float gx1 = qn.y - qc.y, gy1 = qr - qc.y;
-    const float i0 = rcp_approx(fmaf(tau, sqrt_approx(fmaf(gx0, gx0, gy0 * gy0)), 1.f));
-    const float i1 = rcp_approx(fmaf(tau, sqrt_approx(fmaf(gx1, gx1, gy1 * gy1)), 1.f));
-    p2c = make_float2(fmaf(tau, gy0, p2c.x) * i0, fmaf(tau, gy1, p2c.y) * i1);
-    return make_float2(fmaf(tau, gx0, pc.x) * i0, fmaf(tau, gx1, pc.y) * i1);
+    return chambolle_tail(sub2(qn, qc), sub2(make_float2(qc.y, qr), qc), pc, tau, p2c);
+}
+
+// q = div p - g / theta at a lane's two columns of one row, from p1 of the row
+// (p1c) and of the row above (pu), p2 of the row (p2c) and p2 of the column to
+// the left of the lane's first column (p2l).
+__device__ __forceinline__ float2 q_pair(float2 p1c, float2 pu, float2 p2c, float p2l, float2 g,
+                                         float inv_theta)
+{
+    const float2 dv = add2(sub2(p1c, pu), sub2(p2c, make_float2(p2l, p2c.x)));
+    return fma2(g, make_float2(-inv_theta, -inv_theta), dv);
 }
 
 // Boundary rows exchanged between the warps of a CTA each step (double-
@@ -88,44 +151,52 @@ struct Bnd {
 
 // ns Chambolle steps on the warp's rows (registers) with one barrier per step.
 // INTERIOR: the CTA's whole region lies inside the image, all masks are one.
+//
+// Only the local rows [lo, hi) must be exact after the last step.  p^{t+1} of
+// a row depends on p^t of the rows above and below, so step t (of ns) must be
+// exact on [lo - e, hi + e) with e = ns - 1 - t, a band that narrows by one
+// row per side and step.  A warp whose rows (local rows 1 + wp RPW ..
+// (wp + 1) RPW) miss that band skips the step (it still takes the barrier);
+// the stale rows it leaves, in registers and in the boundary-row buffers, are
+// read only by rows outside the band of the next step, so the rows that
+// matter get exactly the values of a full update.
 template <bool INTERIOR, int B, int RPW>
 __device__ __forceinline__ void sweep_steps(Bnd<B> &sb, float2 (&p1)[RPW], float2 (&p2)[RPW],
                                             const float2 (&g)[RPW], float2 gdn,
                                             const float (&mr)[RPW], float mc0, float mc1,
-                                            float inv_theta, float tau, int ns, int wp, int lane)
+                                            float inv_theta, float tau, int ns, int wp, int lane,
+                                            int lo, int hi)
 {
     constexpr unsigned FULL = 0xffffffffu;
+    const int r0 = 1 + wp * RPW;
     for (int t = 0; t < ns; ++t) {
         const int par = t & 1, nxt = par ^ 1;
-        const float2 pu0 = sb.up[par][wp][lane];
-        const float2 dn1 = sb.dn1[par][wp][lane], dn2 = sb.dn2[par][wp][lane];
-        float2 q[RPW + 1];
+        const int e = ns - 1 - t;
+        if (r0 + RPW > lo - e && r0 < hi + e) {
+            const float2 pu0 = sb.up[par][wp][lane];
+            const float2 dn1 = sb.dn1[par][wp][lane], dn2 = sb.dn2[par][wp][lane];
+            float2 q[RPW + 1];
 #pragma unroll
-        for (int i = 0; i < RPW; ++i) {
-            const float p2l = __shfl_up_sync(FULL, p2[i].y, 1);
-            const float2 pu = i == 0 ? pu0 : p1[i - 1];
-            q[i].x = fmaf(-g[i].x, inv_theta, (p1[i].x - pu.x) + (p2[i].x - p2l));
-            q[i].y = fmaf(-g[i].y, inv_theta, (p1[i].y - pu.y) + (p2[i].y - p2[i].x));
-        }
-        {
-            const float p2l = __shfl_up_sync(FULL, dn2.y, 1);
-            q[RPW].x = fmaf(-gdn.x, inv_theta, (dn1.x - p1[RPW - 1].x) + (dn2.x - p2l));
-            q[RPW].y = fmaf(-gdn.y, inv_theta, (dn1.y - p1[RPW - 1].y) + (dn2.y - dn2.x));
-        }
+            for (int i = 0; i < RPW; ++i)
+                q[i] = q_pair(p1[i], i == 0 ? pu0 : p1[i - 1], p2[i],
+                              __shfl_up_sync(FULL, p2[i].y, 1), g[i], inv_theta);
+            q[RPW] = q_pair(dn1, p1[RPW - 1], dn2, __shfl_up_sync(FULL, dn2.y, 1), gdn, inv_theta);
 #pragma unroll
-        for (int i = 0; i < RPW; ++i) {
-            const float qr = __shfl_down_sync(FULL, q[i].x, 1);
-            float2 p2n = p2[i];
-            const float2 p1n =
-                INTERIOR ? chambolle_pair_interior(q[i], q[i + 1], qr, p1[i], tau, p2n)
-                         : chambolle_pair(q[i], q[i + 1], qr, p1[i], mr[i], mc0, mc1, tau, p2n);
-            p1[i] = p1n;
-            p2[i] = p2n;
-        }
-        if (wp + 1 < B) sb.up[nxt][wp + 1][lane] = p1[RPW - 1];
-        if (wp > 0) {
-            sb.dn1[nxt][wp - 1][lane] = p1[0];
-            sb.dn2[nxt][wp - 1][lane] = p2[0];
+            for (int i = 0; i < RPW; ++i) {
+                const float qr = __shfl_down_sync(FULL, q[i].x, 1);
+                float2 p2n = p2[i];
+                const float2 p1n =
+                    INTERIOR ? chambolle_pair_interior(q[i], q[i + 1], qr, p1[i], tau, p2n)
+                             : chambolle_pair(q[i], q[i + 1], qr, p1[i], mr[i], mc0, mc1, tau,
+                                              p2n);
+                p1[i] = p1n;
+                p2[i] = p2n;
+            }
+            if (wp + 1 < B) sb.up[nxt][wp + 1][lane] = p1[RPW - 1];
+            if (wp > 0) {
+                sb.dn1[nxt][wp - 1][lane] = p1[0];
+                sb.dn2[nxt][wp - 1][lane] = p2[0];
+            }
         }
         __syncthreads();
     }
@@ -150,8 +221,7 @@ __device__ __forceinline__ void tv_band_rows(const float *A1, const float *A2, c
         const float2 p1u = *reinterpret_cast<const float2 *>(a1 - PW);
         const float2 gc = *reinterpret_cast<const float2 *>(gg);
         const float p2l = reinterpret_cast<const float2 *>(a2 - 2)->y;
-        qc.x = fmaf(-gc.x, inv_theta, (p1c.x - p1u.x) + (p2c.x - p2l));
-        qc.y = fmaf(-gc.y, inv_theta, (p1c.y - p1u.y) + (p2c.y - p2c.x));
+        qc = q_pair(p1c, p1u, p2c, p2l, gc, inv_theta);
     }
     for (int i = r0; i < r1; ++i, ++gi) {
         a1 += PW;
@@ -161,9 +231,7 @@ __device__ __forceinline__ void tv_band_rows(const float *A1, const float *A2, c
         const float2 p2n = *reinterpret_cast<const float2 *>(a2);
         const float2 gn = *reinterpret_cast<const float2 *>(gg);
         const float p2l = reinterpret_cast<const float2 *>(a2 - 2)->y;
-        float2 qn;
-        qn.x = fmaf(-gn.x, inv_theta, (p1n.x - p1c.x) + (p2n.x - p2l));
-        qn.y = fmaf(-gn.y, inv_theta, (p1n.y - p1c.y) + (p2n.y - p2n.x));
+        const float2 qn = q_pair(p1n, p1c, p2n, p2l, gn, inv_theta);
         const float qr = __shfl_down_sync(0xffffffffu, qc.x, 1);
         const float mr = gi < Hm1 ? 1.f : 0.f;
         float2 p2new = p2c;
