@@ -279,23 +279,74 @@ __global__ void prox_out_bwd_kernel(const float *__restrict__ P, Geo g, float th
     block_acc(tb, acc, 2);
 }
 
-// Reverse of one dual step, part 1: abar = J_proj(a)^T pbar^{t+1}; the kappa
-// term's theta partial: dkappa = -tau <abar, p>, dtheta += dkappa * (-eps/theta^2).
-__global__ void dual_bwd_a_kernel(const DualArgs A, const float *__restrict__ Pbar_next,
-                                  float *__restrict__ Abar, float eps, double *__restrict__ acc)
+// Reverse of one dual step p^{t+1} = proj(a), a = p^t + tau (grad q - kappa
+// p^t), q = div p^t - h / theta.  Given pbar^{t+1}:
+//   abar  = J_proj(a)^T pbar^{t+1}   (J = (I - a a^T / |a|^2) / |a| if |a| > 1)
+//   qbar  = tau grad^T abar = -tau div abar
+//   pbar^t = (1 - tau kappa) abar - grad qbar,  hbar -= qbar / theta,
+// and the theta partials: kappa = eps / theta gives -tau <abar, p^t> (-eps /
+// theta^2), the h / theta term gives <qbar, h> / theta^2.
+// One pass: a CTA owns a 32 x 32 tile of one batch item and keeps a 36 x 36
+// region (2 pixels of halo above / left, 2 below / right) in shared memory:
+// q on the region, abar where qbar needs it, qbar one row / column beyond the
+// tile, then pbar^t and hbar on the tile; abar never leaves the chip.  The
+// theta partials are summed over the tile's own pixels only.
+constexpr int kDT = 32;              // tile side
+constexpr int kDR = kDT + 4;         // region side
+constexpr int kDP = kDR + 1;         // row pitch (bank offset)
+
+__global__ void __launch_bounds__(kT) dual_bwd_kernel(const DualArgs A,
+                                                      const float *__restrict__ Pbar_next,
+                                                      float *__restrict__ Pbar,
+                                                      float *__restrict__ Hbar, float eps,
+                                                      double *__restrict__ acc)
 {
-    const size_t p = blockIdx.x * (size_t)kT + threadIdx.x;
-    const int bi = blockIdx.y;
+    __shared__ float sp1[kDR][kDP], sp2[kDR][kDP], sh[kDR][kDP], sb1[kDR][kDP], sb2[kDR][kDP];
+    __shared__ float sq[kDR][kDP], sa1[kDR][kDP], sa2[kDR][kDP], sqb[kDR][kDP];
     const Geo &g = A.g;
+    const int H = g.H, W = g.W;
+    const int tx = (W + kDT - 1) / kDT;
+    const int i0 = (int)(blockIdx.x / tx) * kDT, j0 = (int)(blockIdx.x % tx) * kDT;
+    const int bi = blockIdx.y;
+    const size_t HW = g.HW();
+    const float *p1 = A.P + (size_t)bi * 2 * HW, *p2 = p1 + HW;
+    const float *h = A.Hb + (size_t)bi * HW;
+    const float *n1 = Pbar_next + (size_t)bi * 2 * HW, *n2 = n1 + HW;
+    // local (li, lj) is image (i0 - 2 + li, j0 - 2 + lj); outside the image 0
+    for (int x = threadIdx.x; x < kDR * kDR; x += kT) {
+        const int li = x / kDR, lj = x % kDR;
+        const int i = i0 - 2 + li, j = j0 - 2 + lj;
+        const bool in = i >= 0 && i < H && j >= 0 && j < W;
+        const size_t o = in ? (size_t)i * W + j : 0;
+        sp1[li][lj] = in ? p1[o] : 0.f;
+        sp2[li][lj] = in ? p2[o] : 0.f;
+        sh[li][lj] = in ? h[o] : 0.f;
+        sb1[li][lj] = in ? n1[o] : 0.f;
+        sb2[li][lj] = in ? n2[o] : 0.f;
+    }
+    __syncthreads();
+    // q = div p - h / theta on local rows / columns 1 .. 35 (boundaries as divp)
+    for (int x = threadIdx.x; x < (kDR - 1) * (kDR - 1); x += kT) {
+        const int li = 1 + x / (kDR - 1), lj = 1 + x % (kDR - 1);
+        const int i = i0 - 2 + li, j = j0 - 2 + lj;
+        const float a = (i < H - 1 ? sp1[li][lj] : 0.f) - (i > 0 ? sp1[li - 1][lj] : 0.f);
+        const float c = (j < W - 1 ? sp2[li][lj] : 0.f) - (j > 0 ? sp2[li][lj - 1] : 0.f);
+        sq[li][lj] = (a + c) - sh[li][lj] * A.inv_theta;
+    }
+    __syncthreads();
+    const float theta = 1.f / A.inv_theta;
     double tb = 0.0;
-    if (p < g.HW()) {
-        const int i = (int)(p / g.W), j = (int)(p % g.W);
-        const float *p1 = A.P + (size_t)bi * 2 * g.HW(), *p2 = p1 + g.HW();
-        const float *h = A.Hb + (size_t)bi * g.HW();
-        float a1, a2;
-        dual_a(p1, p2, h, i, j, g.H, g.W, A.inv_theta, A.tau, A.kappa, a1, a2);
-        const float *n1 = Pbar_next + (size_t)bi * 2 * g.HW(), *n2 = n1 + g.HW();
-        const float b1 = n1[p], b2 = n2[p];
+    // abar on local rows / columns 1 .. 34
+    for (int x = threadIdx.x; x < (kDR - 2) * (kDR - 2); x += kT) {
+        const int li = 1 + x / (kDR - 2), lj = 1 + x % (kDR - 2);
+        const int i = i0 - 2 + li, j = j0 - 2 + lj;
+        const float qc = sq[li][lj];
+        const float gx = i < H - 1 ? sq[li + 1][lj] - qc : 0.f;
+        const float gy = j < W - 1 ? sq[li][lj + 1] - qc : 0.f;
+        const float pc1 = sp1[li][lj], pc2 = sp2[li][lj];
+        const float a1 = pc1 + A.tau * (gx - A.kappa * pc1);
+        const float a2 = pc2 + A.tau * (gy - A.kappa * pc2);
+        const float b1 = sb1[li][lj], b2 = sb2[li][lj];
         const float na = sqrtf(a1 * a1 + a2 * a2);
         float o1 = b1, o2 = b2;
         if (na > 1.f) {  // J = (I - a a^T / |a|^2) / |a|, symmetric
@@ -303,47 +354,39 @@ __global__ void dual_bwd_a_kernel(const DualArgs A, const float *__restrict__ Pb
             o1 = (b1 - a1 * dot) / na;
             o2 = (b2 - a2 * dot) / na;
         }
-        float *ab1 = Abar + (size_t)bi * 2 * g.HW(), *ab2 = ab1 + g.HW();
-        ab1[p] = o1;
-        ab2[p] = o2;
-        const float kbar = -A.tau * (o1 * p1[p] + o2 * p2[p]);
-        const float theta = 1.f / A.inv_theta;
-        tb = (double)(kbar * (-eps / (theta * theta)));
+        sa1[li][lj] = o1;
+        sa2[li][lj] = o2;
+        if (li >= 2 && li < kDT + 2 && lj >= 2 && lj < kDT + 2 && i < H && j < W) {
+            const float kbar = -A.tau * (o1 * pc1 + o2 * pc2);
+            tb += (double)(kbar * (-eps / (theta * theta)));
+        }
     }
-    block_acc(tb, acc, 2);
-}
-
-// qbar = tau * grad^T abar = -tau div abar (a depends on q through tau grad q).
-__device__ __forceinline__ float qbar_at(const float *ab1, const float *ab2, int i, int j, int H,
-                                         int W, float tau)
-{
-    return -tau * divp(ab1, ab2, i, j, H, W);
-}
-
-// Reverse of one dual step, part 2: pbar^t = (1 - tau kappa) abar - grad qbar;
-// hbar -= qbar / theta; theta partial <qbar, h> / theta^2.
-__global__ void dual_bwd_b_kernel(const DualArgs A, const float *__restrict__ Abar,
-                                  float *__restrict__ Pbar, float *__restrict__ Hbar,
-                                  double *__restrict__ acc)
-{
-    const size_t p = blockIdx.x * (size_t)kT + threadIdx.x;
-    const int bi = blockIdx.y;
-    const Geo &g = A.g;
-    double tb = 0.0;
-    if (p < g.HW()) {
-        const int i = (int)(p / g.W), j = (int)(p % g.W);
-        const float *ab1 = Abar + (size_t)bi * 2 * g.HW(), *ab2 = ab1 + g.HW();
-        const float qc = qbar_at(ab1, ab2, i, j, g.H, g.W, A.tau);
-        const float gx = i < g.H - 1 ? qbar_at(ab1, ab2, i + 1, j, g.H, g.W, A.tau) - qc : 0.f;
-        const float gy = j < g.W - 1 ? qbar_at(ab1, ab2, i, j + 1, g.H, g.W, A.tau) - qc : 0.f;
-        const float damp = 1.f - A.tau * A.kappa;
-        float *pb1 = Pbar + (size_t)bi * 2 * g.HW(), *pb2 = pb1 + g.HW();
-        // q = div p - h/theta: dq/dp = div, so pbar += div^T qbar = -grad qbar
-        pb1[p] = damp * ab1[p] - gx;
-        pb2[p] = damp * ab2[p] - gy;
-        const float hv = A.Hb[bi * g.HW() + p];
-        Hbar[bi * g.HW() + p] -= qc * A.inv_theta;
-        tb = (double)(qc * hv * A.inv_theta * A.inv_theta);
+    __syncthreads();
+    // qbar = -tau div abar on local rows / columns 2 .. 34
+    for (int x = threadIdx.x; x < (kDT + 1) * (kDT + 1); x += kT) {
+        const int li = 2 + x / (kDT + 1), lj = 2 + x % (kDT + 1);
+        const int i = i0 - 2 + li, j = j0 - 2 + lj;
+        const float a = (i < H - 1 ? sa1[li][lj] : 0.f) - (i > 0 ? sa1[li - 1][lj] : 0.f);
+        const float c = (j < W - 1 ? sa2[li][lj] : 0.f) - (j > 0 ? sa2[li][lj - 1] : 0.f);
+        sqb[li][lj] = -A.tau * (a + c);
+    }
+    __syncthreads();
+    // pbar^t = (1 - tau kappa) abar - grad qbar; hbar -= qbar / theta
+    const float damp = 1.f - A.tau * A.kappa;
+    float *pb1 = Pbar + (size_t)bi * 2 * HW, *pb2 = pb1 + HW;
+    float *hb = Hbar + (size_t)bi * HW;
+    for (int x = threadIdx.x; x < kDT * kDT; x += kT) {
+        const int li = 2 + x / kDT, lj = 2 + x % kDT;
+        const int i = i0 - 2 + li, j = j0 - 2 + lj;
+        if (i >= H || j >= W) continue;
+        const size_t o = (size_t)i * W + j;
+        const float qc = sqb[li][lj];
+        const float gx = i < H - 1 ? sqb[li + 1][lj] - qc : 0.f;
+        const float gy = j < W - 1 ? sqb[li][lj + 1] - qc : 0.f;
+        pb1[o] = damp * sa1[li][lj] - gx;
+        pb2[o] = damp * sa2[li][lj] - gy;
+        hb[o] -= qc * A.inv_theta;
+        tb += (double)(qc * sh[li][lj] * A.inv_theta * A.inv_theta);
     }
     block_acc(tb, acc, 2);
 }
@@ -359,7 +402,7 @@ __global__ void axpy_kernel(float *__restrict__ y, const float *__restrict__ x, 
 // ---- host side ---------------------------------------------------------------
 struct Ws {
     float *U, *D, *Wb, *Hb, *Pa, *Pb, *PH, *Useg, *Dseg;
-    float *Ubar_new, *Ubar_old, *Wbar, *Dbar, *Hbar, *Pbar_a, *Pbar_b, *Abar;
+    float *Ubar_new, *Ubar_old, *Wbar, *Dbar, *Hbar, *Pbar_a, *Pbar_b;
     double *acc;  // [3]: rho (direct), gamma (direct), theta (total)
 };
 
@@ -369,7 +412,7 @@ size_t ws_bytes(const Geo &g, int T, int S)
 {
     const size_t nv = (size_t)g.B * g.NV() * 4, hw = (size_t)g.B * g.HW() * 4;
     return al(nv) * 3 + al(hw) + 2 * al(2 * hw) + al((size_t)(T + 1) * 2 * hw) +
-           2 * al((size_t)(S + 1) * nv) + al(nv) * 4 + al(hw) + 3 * al(2 * hw) +
+           2 * al((size_t)(S + 1) * nv) + al(nv) * 4 + al(hw) + 2 * al(2 * hw) +
            al(3 * kAccCopies * sizeof(double));
 }
 
@@ -399,7 +442,6 @@ Ws carve(void *base, const Geo &g, int T, int S)
     w.Hbar = take(hw);
     w.Pbar_a = take(2 * hw);
     w.Pbar_b = take(2 * hw);
-    w.Abar = take(2 * hw);
     w.acc = (double *)take(3 * kAccCopies * sizeof(double));
     return w;
 }
@@ -562,13 +604,12 @@ cslsm_status unrolled_backward(int B, int Z, int H, int W, float rho, float lam,
                                    pT, g, theta, w.Ubar_new + off, w.Hbar, w.Pbar_a, w.acc));
                 const int Tn = theta > 0.f ? T : 0;
                 float *pb_in = w.Pbar_a, *pb_out = w.Pbar_b;
+                const dim3 tgrid((unsigned)(((W + kDT - 1) / kDT) * ((H + kDT - 1) / kDT)), B);
                 for (int t = Tn - 1; t >= 0; --t) {
                     DualArgs Ad{w.PH + (size_t)t * hw2, nullptr, w.Hb, g, 1.f / theta, tau,
                                 eps / theta};
-                    LAUNCH(K_DIFF, dual_bwd_a_kernel<<<pgrid(g), kT, 0, s>>>(Ad, pb_in, w.Abar, eps,
-                                                                             w.acc));
-                    LAUNCH(K_DIFF, dual_bwd_b_kernel<<<pgrid(g), kT, 0, s>>>(Ad, w.Abar, pb_out,
-                                                                             w.Hbar, w.acc));
+                    LAUNCH(K_DIFF, dual_bwd_kernel<<<tgrid, kT, 0, s>>>(Ad, pb_in, pb_out, w.Hbar,
+                                                                         eps, w.acc));
                     std::swap(pb_in, pb_out);
                 }
                 LAUNCH(K_DIFF, hform_bwd_kernel<<<pgrid(g), kT, 0, s>>>(

@@ -38,7 +38,7 @@ def _scalars(rho=0.9, lam=0.05, gamma=0.2, dev="cuda", dtype=torch.float32):
     return [torch.tensor(v, dtype=dtype, device=dev, requires_grad=True) for v in (rho, lam, gamma)]
 
 
-@pytest.mark.parametrize("B,Z,H,W", [(2, 4, 24, 20), (1, 3, 17, 33), (1, 2, 40, 9)])
+@pytest.mark.parametrize("B,Z,H,W", [(2, 4, 24, 20), (1, 3, 17, 33), (1, 2, 40, 9), (1, 3, 70, 45)])
 def test_forward_and_gradient_match_fp64_oracle(cs, B, Z, H, W):
     logits, b, x = _problem(B + Z + H, B, Z, H, W)
     vbar = torch.randn(B, Z, H, W, generator=torch.Generator().manual_seed(4))
