@@ -301,8 +301,12 @@ __global__ void __launch_bounds__(kT) dual_bwd_kernel(const DualArgs A,
                                                       float *__restrict__ Hbar, float eps,
                                                       double *__restrict__ acc)
 {
-    __shared__ float sp1[kDR][kDP], sp2[kDR][kDP], sh[kDR][kDP], sb1[kDR][kDP], sb2[kDR][kDP];
-    __shared__ float sq[kDR][kDP], sa1[kDR][kDP], sa2[kDR][kDP], sqb[kDR][kDP];
+    // p^t, overwritten by abar where it is formed (each pixel reads only its own
+    // p there); q, then qbar: 21 KB, eight CTAs per SM
+    __shared__ float sp1[kDR][kDP], sp2[kDR][kDP], sh[kDR][kDP], sq[kDR][kDP];
+    float(&sa1)[kDR][kDP] = sp1;
+    float(&sa2)[kDR][kDP] = sp2;
+    float(&sqb)[kDR][kDP] = sq;
     const Geo &g = A.g;
     const int H = g.H, W = g.W;
     const int tx = (W + kDT - 1) / kDT;
@@ -321,8 +325,6 @@ __global__ void __launch_bounds__(kT) dual_bwd_kernel(const DualArgs A,
         sp1[li][lj] = in ? p1[o] : 0.f;
         sp2[li][lj] = in ? p2[o] : 0.f;
         sh[li][lj] = in ? h[o] : 0.f;
-        sb1[li][lj] = in ? n1[o] : 0.f;
-        sb2[li][lj] = in ? n2[o] : 0.f;
     }
     __syncthreads();
     // q = div p - h / theta on local rows / columns 1 .. 35 (boundaries as divp)
@@ -346,7 +348,9 @@ __global__ void __launch_bounds__(kT) dual_bwd_kernel(const DualArgs A,
         const float pc1 = sp1[li][lj], pc2 = sp2[li][lj];
         const float a1 = pc1 + A.tau * (gx - A.kappa * pc1);
         const float a2 = pc2 + A.tau * (gy - A.kappa * pc2);
-        const float b1 = sb1[li][lj], b2 = sb2[li][lj];
+        const bool in = i >= 0 && i < H && j >= 0 && j < W;
+        const size_t o = in ? (size_t)i * W + j : 0;
+        const float b1 = in ? n1[o] : 0.f, b2 = in ? n2[o] : 0.f;
         const float na = sqrtf(a1 * a1 + a2 * a2);
         float o1 = b1, o2 = b2;
         if (na > 1.f) {  // J = (I - a a^T / |a|^2) / |a|, symmetric
