@@ -222,21 +222,26 @@ __device__ __forceinline__ void dual_a(const float *p1, const float *p2, const f
     a2 = p2[o] + tau * (gy - kappa * p2[o]);
 }
 
-__global__ void dual_fwd_kernel(const DualArgs A)
+// One thread per pixel on a 2-D grid: blocks of 32 columns x 8 rows (rows
+// grid-strided), z = batch item.
+__global__ void __launch_bounds__(kT) dual_fwd_kernel(const DualArgs A)
 {
-    const size_t p = blockIdx.x * (size_t)kT + threadIdx.x;
-    const int bi = blockIdx.y;
     const Geo &g = A.g;
-    if (p >= g.HW()) return;
-    const int i = (int)(p / g.W), j = (int)(p % g.W);
+    const int j = (int)blockIdx.x * 32 + (int)(threadIdx.x & 31);
+    const int bi = blockIdx.z;
+    if (j >= g.W) return;
     const float *p1 = A.P + (size_t)bi * 2 * g.HW(), *p2 = p1 + g.HW();
     const float *h = A.Hb + (size_t)bi * g.HW();
-    float a1, a2;
-    dual_a(p1, p2, h, i, j, g.H, g.W, A.inv_theta, A.tau, A.kappa, a1, a2);
-    const float sc = 1.f / fmaxf(1.f, sqrtf(a1 * a1 + a2 * a2));
     float *n1 = A.Pn + (size_t)bi * 2 * g.HW(), *n2 = n1 + g.HW();
-    n1[p] = a1 * sc;
-    n2[p] = a2 * sc;
+    for (int i = (int)blockIdx.y * (kT / 32) + (int)(threadIdx.x >> 5); i < g.H;
+         i += (int)gridDim.y * (kT / 32)) {
+        const int p = i * g.W + j;  // H W < 2^31
+        float a1, a2;
+        dual_a(p1, p2, h, i, j, g.H, g.W, A.inv_theta, A.tau, A.kappa, a1, a2);
+        const float sc = 1.f / fmaxf(1.f, sqrtf(a1 * a1 + a2 * a2));
+        n1[p] = a1 * sc;
+        n2[p] = a2 * sc;
+    }
 }
 
 // u_n = h - theta div p; d_n = w_n - u_n.
@@ -457,6 +462,11 @@ struct Prm {
 };
 
 inline dim3 pgrid(const Geo &g) { return dim3((unsigned)((g.HW() + kT - 1) / kT), g.B); }
+inline dim3 grid2d(const Geo &g)
+{
+    const int rows = (g.H + kT / 32 - 1) / (kT / 32);
+    return dim3((unsigned)((g.W + 31) / 32), (unsigned)std::min(rows, 65535), g.B);
+}
 
 #define LAUNCH(kid, ...)                    \
     do {                                    \
@@ -487,7 +497,7 @@ cslsm_status slice_prox(const Geo &g, const Prm &P, const float *Hb, float *Pa, 
     for (int t = 0; t < T; ++t) {
         float *nxt = PH ? PH + (size_t)(t + 1) * hw2 : (cur == Pa ? Pb : Pa);
         DualArgs A{cur, nxt, Hb, g, 1.f / theta, P.tau, P.eps / theta};
-        LAUNCH(K_DIFF, dual_fwd_kernel<<<pgrid(g), kT, 0, s>>>(A));
+        LAUNCH(K_DIFF, dual_fwd_kernel<<<grid2d(g), kT, 0, s>>>(A));
         cur = nxt;
     }
     *pT = cur;
