@@ -291,14 +291,16 @@ __global__ void prox_out_bwd_kernel(const float *__restrict__ P, Geo g, float th
 //   pbar^t = (1 - tau kappa) abar - grad qbar,  hbar -= qbar / theta,
 // and the theta partials: kappa = eps / theta gives -tau <abar, p^t> (-eps /
 // theta^2), the h / theta term gives <qbar, h> / theta^2.
-// One pass: a CTA owns a 32 x 32 tile of one batch item and keeps a 36 x 36
-// region (2 pixels of halo above / left, 2 below / right) in shared memory:
-// q on the region, abar where qbar needs it, qbar one row / column beyond the
-// tile, then pbar^t and hbar on the tile; abar never leaves the chip.  The
-// theta partials are summed over the tile's own pixels only.
-constexpr int kDT = 32;              // tile side
-constexpr int kDR = kDT + 4;         // region side
-constexpr int kDP = kDR + 1;         // row pitch (bank offset)
+// One pass: a CTA owns a 28 x 28 tile of one batch item and keeps a 32 x 32
+// region (2 pixels of halo on every side) in shared memory, one region column
+// per lane and kRB rows per warp: q on the region, abar where qbar needs it,
+// qbar one row / column beyond the tile, then pbar^t and hbar on the tile;
+// abar never leaves the chip.  The theta partials are summed over the tile's
+// own pixels only (in FP32 per thread, FP64 from the block sum on).
+constexpr int kBT = 28;              // tile side
+constexpr int kDR = kBT + 4;         // region side: one warp's 32 lanes
+constexpr int kDP = kDR + 1;         // row pitch
+static_assert(kDR == 32, "one region column per lane");
 
 __global__ void __launch_bounds__(kT) dual_bwd_kernel(const DualArgs A,
                                                       const float *__restrict__ Pbar_next,
@@ -307,97 +309,106 @@ __global__ void __launch_bounds__(kT) dual_bwd_kernel(const DualArgs A,
                                                       double *__restrict__ acc)
 {
     // p^t, overwritten by abar where it is formed (each pixel reads only its own
-    // p there); q, then qbar: 21 KB, eight CTAs per SM
+    // p there); q, then qbar
     __shared__ float sp1[kDR][kDP], sp2[kDR][kDP], sh[kDR][kDP], sq[kDR][kDP];
     float(&sa1)[kDR][kDP] = sp1;
     float(&sa2)[kDR][kDP] = sp2;
     float(&sqb)[kDR][kDP] = sq;
+    constexpr int kW = kT / 32;  // warps
     const Geo &g = A.g;
     const int H = g.H, W = g.W;
-    const int tx = (W + kDT - 1) / kDT;
-    const int i0 = (int)(blockIdx.x / tx) * kDT, j0 = (int)(blockIdx.x % tx) * kDT;
+    const int tx = (W + kBT - 1) / kBT;
+    const int i0 = (int)(blockIdx.x / tx) * kBT, j0 = (int)(blockIdx.x % tx) * kBT;
     const int bi = blockIdx.y;
+    const int lj = (int)(threadIdx.x & 31), wr = (int)(threadIdx.x >> 5);
+    const int j = j0 - 2 + lj;  // the lane's image column
+    const bool cin = j >= 0 && j < W;
     const size_t HW = g.HW();
     const float *p1 = A.P + (size_t)bi * 2 * HW, *p2 = p1 + HW;
     const float *h = A.Hb + (size_t)bi * HW;
     const float *n1 = Pbar_next + (size_t)bi * 2 * HW, *n2 = n1 + HW;
     // local (li, lj) is image (i0 - 2 + li, j0 - 2 + lj); outside the image 0
-    for (int x = threadIdx.x; x < kDR * kDR; x += kT) {
-        const int li = x / kDR, lj = x % kDR;
-        const int i = i0 - 2 + li, j = j0 - 2 + lj;
-        const bool in = i >= 0 && i < H && j >= 0 && j < W;
-        const size_t o = in ? (size_t)i * W + j : 0;
+    for (int li = wr; li < kDR; li += kW) {
+        const int i = i0 - 2 + li;
+        const bool in = cin && i >= 0 && i < H;
+        const int o = in ? i * W + j : 0;  // H W < 2^31
         sp1[li][lj] = in ? p1[o] : 0.f;
         sp2[li][lj] = in ? p2[o] : 0.f;
         sh[li][lj] = in ? h[o] : 0.f;
     }
     __syncthreads();
-    // q = div p - h / theta on local rows / columns 1 .. 35 (boundaries as divp)
-    for (int x = threadIdx.x; x < (kDR - 1) * (kDR - 1); x += kT) {
-        const int li = 1 + x / (kDR - 1), lj = 1 + x % (kDR - 1);
-        const int i = i0 - 2 + li, j = j0 - 2 + lj;
-        const float a = (i < H - 1 ? sp1[li][lj] : 0.f) - (i > 0 ? sp1[li - 1][lj] : 0.f);
-        const float c = (j < W - 1 ? sp2[li][lj] : 0.f) - (j > 0 ? sp2[li][lj - 1] : 0.f);
-        sq[li][lj] = (a + c) - sh[li][lj] * A.inv_theta;
+    // q = div p - h / theta on local rows / columns 1 .. 31 (boundaries as divp)
+    if (lj >= 1) {
+        for (int li = 1 + wr; li < kDR; li += kW) {
+            const int i = i0 - 2 + li;
+            const float a = (i < H - 1 ? sp1[li][lj] : 0.f) - (i > 0 ? sp1[li - 1][lj] : 0.f);
+            const float c = (j < W - 1 ? sp2[li][lj] : 0.f) - (j > 0 ? sp2[li][lj - 1] : 0.f);
+            sq[li][lj] = (a + c) - sh[li][lj] * A.inv_theta;
+        }
     }
     __syncthreads();
     const float theta = 1.f / A.inv_theta;
-    double tb = 0.0;
-    // abar on local rows / columns 1 .. 34
-    for (int x = threadIdx.x; x < (kDR - 2) * (kDR - 2); x += kT) {
-        const int li = 1 + x / (kDR - 2), lj = 1 + x % (kDR - 2);
-        const int i = i0 - 2 + li, j = j0 - 2 + lj;
-        const float qc = sq[li][lj];
-        const float gx = i < H - 1 ? sq[li + 1][lj] - qc : 0.f;
-        const float gy = j < W - 1 ? sq[li][lj + 1] - qc : 0.f;
-        const float pc1 = sp1[li][lj], pc2 = sp2[li][lj];
-        const float a1 = pc1 + A.tau * (gx - A.kappa * pc1);
-        const float a2 = pc2 + A.tau * (gy - A.kappa * pc2);
-        const bool in = i >= 0 && i < H && j >= 0 && j < W;
-        const size_t o = in ? (size_t)i * W + j : 0;
-        const float b1 = in ? n1[o] : 0.f, b2 = in ? n2[o] : 0.f;
-        const float na = sqrtf(a1 * a1 + a2 * a2);
-        float o1 = b1, o2 = b2;
-        if (na > 1.f) {  // J = (I - a a^T / |a|^2) / |a|, symmetric
-            const float dot = (a1 * b1 + a2 * b2) / (na * na);
-            o1 = (b1 - a1 * dot) / na;
-            o2 = (b2 - a2 * dot) / na;
-        }
-        sa1[li][lj] = o1;
-        sa2[li][lj] = o2;
-        if (li >= 2 && li < kDT + 2 && lj >= 2 && lj < kDT + 2 && i < H && j < W) {
-            const float kbar = -A.tau * (o1 * pc1 + o2 * pc2);
-            tb += (double)(kbar * (-eps / (theta * theta)));
+    const float kfac = -A.tau * (-eps / (theta * theta));
+    const bool ctile = lj >= 2 && lj < kBT + 2 && j < W;
+    float tk = 0.f, tq = 0.f;  // this thread's theta partials (tile pixels)
+    // abar on local rows / columns 1 .. 30
+    if (lj >= 1 && lj < kDR - 1) {
+        for (int li = 1 + wr; li < kDR - 1; li += kW) {
+            const int i = i0 - 2 + li;
+            const float qc = sq[li][lj];
+            const float gx = i < H - 1 ? sq[li + 1][lj] - qc : 0.f;
+            const float gy = j < W - 1 ? sq[li][lj + 1] - qc : 0.f;
+            const float pc1 = sp1[li][lj], pc2 = sp2[li][lj];
+            const float a1 = pc1 + A.tau * (gx - A.kappa * pc1);
+            const float a2 = pc2 + A.tau * (gy - A.kappa * pc2);
+            const bool in = cin && i >= 0 && i < H;
+            const int o = in ? i * W + j : 0;
+            const float b1 = in ? n1[o] : 0.f, b2 = in ? n2[o] : 0.f;
+            const float na = sqrtf(a1 * a1 + a2 * a2);
+            float o1 = b1, o2 = b2;
+            if (na > 1.f) {  // J = (I - a a^T / |a|^2) / |a|, symmetric
+                const float inv = 1.f / na;
+                const float dot = (a1 * b1 + a2 * b2) * inv * inv;
+                o1 = (b1 - a1 * dot) * inv;
+                o2 = (b2 - a2 * dot) * inv;
+            }
+            sa1[li][lj] = o1;
+            sa2[li][lj] = o2;
+            // kappa = eps / theta: d/dtheta of -tau kappa <abar, p>
+            if (ctile && li >= 2 && li < kBT + 2 && i < H) tk += o1 * pc1 + o2 * pc2;
         }
     }
     __syncthreads();
-    // qbar = -tau div abar on local rows / columns 2 .. 34
-    for (int x = threadIdx.x; x < (kDT + 1) * (kDT + 1); x += kT) {
-        const int li = 2 + x / (kDT + 1), lj = 2 + x % (kDT + 1);
-        const int i = i0 - 2 + li, j = j0 - 2 + lj;
-        const float a = (i < H - 1 ? sa1[li][lj] : 0.f) - (i > 0 ? sa1[li - 1][lj] : 0.f);
-        const float c = (j < W - 1 ? sa2[li][lj] : 0.f) - (j > 0 ? sa2[li][lj - 1] : 0.f);
-        sqb[li][lj] = -A.tau * (a + c);
+    // qbar = -tau div abar on local rows / columns 2 .. 30
+    if (lj >= 2 && lj < kDR - 1) {
+        for (int li = 2 + wr; li < kDR - 1; li += kW) {
+            const int i = i0 - 2 + li;
+            const float a = (i < H - 1 ? sa1[li][lj] : 0.f) - (i > 0 ? sa1[li - 1][lj] : 0.f);
+            const float c = (j < W - 1 ? sa2[li][lj] : 0.f) - (j > 0 ? sa2[li][lj - 1] : 0.f);
+            sqb[li][lj] = -A.tau * (a + c);
+        }
     }
     __syncthreads();
-    // pbar^t = (1 - tau kappa) abar - grad qbar; hbar -= qbar / theta
+    // pbar^t = (1 - tau kappa) abar - grad qbar; hbar -= qbar / theta (tile)
     const float damp = 1.f - A.tau * A.kappa;
     float *pb1 = Pbar + (size_t)bi * 2 * HW, *pb2 = pb1 + HW;
     float *hb = Hbar + (size_t)bi * HW;
-    for (int x = threadIdx.x; x < kDT * kDT; x += kT) {
-        const int li = 2 + x / kDT, lj = 2 + x % kDT;
-        const int i = i0 - 2 + li, j = j0 - 2 + lj;
-        if (i >= H || j >= W) continue;
-        const size_t o = (size_t)i * W + j;
-        const float qc = sqb[li][lj];
-        const float gx = i < H - 1 ? sqb[li + 1][lj] - qc : 0.f;
-        const float gy = j < W - 1 ? sqb[li][lj + 1] - qc : 0.f;
-        pb1[o] = damp * sa1[li][lj] - gx;
-        pb2[o] = damp * sa2[li][lj] - gy;
-        hb[o] -= qc * A.inv_theta;
-        tb += (double)(qc * sh[li][lj] * A.inv_theta * A.inv_theta);
+    if (ctile) {
+        for (int li = 2 + wr; li < kBT + 2; li += kW) {
+            const int i = i0 - 2 + li;
+            if (i >= H) break;
+            const int o = i * W + j;
+            const float qc = sqb[li][lj];
+            const float gx = i < H - 1 ? sqb[li + 1][lj] - qc : 0.f;
+            const float gy = j < W - 1 ? sqb[li][lj + 1] - qc : 0.f;
+            pb1[o] = damp * sa1[li][lj] - gx;
+            pb2[o] = damp * sa2[li][lj] - gy;
+            hb[o] -= qc * A.inv_theta;
+            tq += qc * sh[li][lj];
+        }
     }
-    block_acc(tb, acc, 2);
+    block_acc((double)tk * (double)kfac + (double)tq * ((double)A.inv_theta * A.inv_theta), acc,
+              2);
 }
 
 // lbar -> dL/dlogits already includes m (1 - m); Uold_bar etc. are plain adds.
@@ -618,7 +629,7 @@ cslsm_status unrolled_backward(int B, int Z, int H, int W, float rho, float lam,
                                    pT, g, theta, w.Ubar_new + off, w.Hbar, w.Pbar_a, w.acc));
                 const int Tn = theta > 0.f ? T : 0;
                 float *pb_in = w.Pbar_a, *pb_out = w.Pbar_b;
-                const dim3 tgrid((unsigned)(((W + kDT - 1) / kDT) * ((H + kDT - 1) / kDT)), B);
+                const dim3 tgrid((unsigned)(((W + kBT - 1) / kBT) * ((H + kBT - 1) / kBT)), B);
                 for (int t = Tn - 1; t >= 0; --t) {
                     DualArgs Ad{w.PH + (size_t)t * hw2, nullptr, w.Hb, g, 1.f / theta, tau,
                                 eps / theta};
