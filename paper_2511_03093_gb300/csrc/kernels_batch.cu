@@ -82,6 +82,19 @@ struct BDesc {
     int T, k, P;  // steps per prox, steps per phase, phases per prox
 };
 
+// Completed-unit counters: read with acquire, incremented with release (gpu scope).
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void red_release_add_u64(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
 __device__ __forceinline__ unsigned long long global_ns()
 {
     unsigned long long t;
@@ -336,7 +349,7 @@ __global__ void __launch_bounds__(kBNT) batch_persistent_kernel(const BDesc *__r
                              : (unsigned long long)((long long)k * it.units_iter +
                                                     level_prefix(it, p));
             const unsigned long long t0 = global_ns();
-            while (*(volatile unsigned long long *)(D.done + i) < need) {
+            while (ld_acquire_u64(D.done + i) < need) {
                 if (*(volatile int *)D.error) {
                     s_abort = 1;
                     break;
@@ -346,9 +359,8 @@ __global__ void __launch_bounds__(kBNT) batch_persistent_kernel(const BDesc *__r
                     s_abort = 1;
                     break;
                 }
-                __nanosleep(128);
+                __nanosleep(32);
             }
-            __threadfence();
         }
         __syncthreads();
         if (s_abort) break;
@@ -369,11 +381,10 @@ __global__ void __launch_bounds__(kBNT) batch_persistent_kernel(const BDesc *__r
             }
             tv_unit<S>(it, D, n, j, tile, sb);
         }
+        // the barrier orders every thread's stores before thread 0's release
+        // add; a unit that acquires the count sees them
         __syncthreads();
-        if (threadIdx.x == 0) {
-            __threadfence();
-            atomicAdd(D.done + i, 1ull);
-        }
+        if (threadIdx.x == 0) red_release_add_u64(D.done + i, 1ull);
     }
 }
 

@@ -14,8 +14,9 @@
 //
 // Ordering: every (slice, phase) pair is an epoch e = n * P + j.  A CTA
 // starts epoch e only after its eight neighbours have completed epoch e - 1
-// (a per-tile flag holding the id of the last completed epoch, written with
-// release semantics after a fence, polled with acquire loads).  Neighbours are
+// (a per-tile flag holding the id of the last completed epoch, written by one
+// thread with release semantics after a CTA barrier, polled with acquire
+// loads).  Neighbours are
 // therefore never more than one epoch apart, which makes the reuse of the two
 // parity buffers of p and the in-place update of u safe: the data a CTA
 // overwrites in epoch e was last read by its neighbours in epoch e - 1 or
@@ -331,10 +332,10 @@ __global__ void __launch_bounds__(B * 32) tvz_sweep_kernel(const ZsArgs a)
                 }
             }
             __syncthreads();
-            if (threadIdx.x == 0) {
-                __threadfence();
-                st_release(a.flags + tile, a.base + 1u + (unsigned)e);
-            }
+            // the barrier orders every thread's stores before thread 0's release
+            // store, whose release semantics make them visible (at gpu scope) to a
+            // neighbour that acquires the flag
+            if (threadIdx.x == 0) st_release(a.flags + tile, a.base + 1u + (unsigned)e);
         }
     }
 }
