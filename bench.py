@@ -524,23 +524,32 @@ def run_secondary(args) -> None:
         b = (torch.sigmoid(logits) * x).sum(1)
         sc = [torch.tensor(v, device=dev, requires_grad=True) for v in (1.0, 0.05, 0.2)]
         lg = logits.clone().requires_grad_(True)
-        fw, bw = [], []
-        for it in range(max(2, args.steps)):
-            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-            e0.record()
-            v = cs.unrolled_admm(lg, b, *sc, iters=30, tv_steps=20, ckpt_every=5)
-            loss = 0.5 * ((v - x) ** 2).mean()
-            e1.record()
-            loss.backward()
-            e2.record()
-            e2.synchronize()
-            if it:
-                fw.append(e0.elapsed_time(e1))
-                bw.append(e1.elapsed_time(e2))
+        def run(keep, n):
+            fw, bw = [], []
+            for it in range(n + 1):
+                e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+                e0.record()
+                v = cs.unrolled_admm(lg, b, *sc, iters=30, tv_steps=20, ckpt_every=5,
+                                     keep_duals=keep)
+                loss = 0.5 * ((v - x) ** 2).mean()
+                e1.record()
+                loss.backward()
+                e2.record()
+                e2.synchronize()
+                if it:
+                    fw.append(e0.elapsed_time(e1))
+                    bw.append(e1.elapsed_time(e2))
+            return float(np.mean(fw)), float(np.mean(bw))
+
+        # dual iterates kept by the segment recompute (29 GB of workspace), then
+        # recomputed per slice in the reverse sweep
+        fwk, bwk = run(True, max(1, args.steps))
+        fwr, bwr = run(False, 1)
         vox = B * Z * H * W
         out.update(metric="unrolled PnP-ADMM voxel-iterations/s (forward + backward)", unit=UNIT,
-                   value=vox * 30 / ((np.mean(fw) + np.mean(bw)) / 1e3), forward_ms=float(np.mean(fw)),
-                   backward_ms=float(np.mean(bw)), batch=B, volume=[Z, H, W], iterations=30)
+                   value=vox * 30 / ((fwk + bwk) / 1e3), forward_ms=fwk, backward_ms=bwk,
+                   backward_ms_recompute_duals=bwr, forward_ms_recompute_run=fwr,
+                   keep_duals=True, batch=B, volume=[Z, H, W], iterations=30)
     elif name == "wnnm_512x512x16":
         # the WNNM prior (listed in Sec. III-B) on the benchmark volume, z term on
         wk = synth.WORKLOADS["tvz_512x512x16"]

@@ -36,7 +36,7 @@ extern "C" {
 #endif
 
 #define CSLSM_MAX_R 32
-#define CSLSM_ABI_VERSION 3
+#define CSLSM_ABI_VERSION 4
 
 typedef enum {
     CSLSM_OK = 0,
@@ -256,10 +256,17 @@ cslsm_status cslsm_batch_destroy(cslsm_batch batch);
  * Layouts: logits, v_out, logits_bar [B][Z][H][W]; b [B][H][W]; ckpt holds
  * ceil(iters / ckpt_every) checkpoints of (u, d): [n_ckpt][2][B][Z][H][W]
  * floats; ws is caller-owned device scratch of cslsm_unrolled_workspace_bytes
- * bytes.  The backward recomputes each checkpoint segment and runs the
+ * bytes (the same params for the workspace size, the forward and the
+ * backward).  The backward recomputes each checkpoint segment and runs the
  * hand-written adjoint; it synchronises `stream` (to combine the scalar
  * gradients) and writes dL/dlogits and scalar_bar (device double[3]) =
- * {dL/drho, dL/dlambda, dL/dgamma} for the given v_bar = dL/dv^K. */
+ * {dL/drho, dL/dlambda, dL/dgamma} for the given v_bar = dL/dv^K.
+ * keep_duals = 1 trades memory for time: the segment recompute keeps every
+ * slice's prox input and its tv_steps + 1 dual iterates, so the reverse sweep
+ * reads them instead of recomputing them (same results bit for bit).  The
+ * workspace then grows by ckpt_every x Z x (2 tv_steps + 3) x B x H x W
+ * floats (29 GB for batch 8 x 512 x 512 x 16, 20 steps, checkpoints every 5
+ * iterations). */
 typedef struct {
     float rho, lambda, gamma; /* rho > 0, lambda > 0, gamma >= 0 */
     int iters;                /* K */
@@ -267,6 +274,7 @@ typedef struct {
     float tv_tau;             /* dual step, (0, 1/8] */
     float huber_eps;          /* >= 0 (0: plain TV) */
     int ckpt_every;           /* checkpoint period in iterations */
+    int keep_duals;           /* 0: recompute the dual iterates in the reverse sweep; 1: keep */
 } cslsm_unrolled_params;
 
 size_t cslsm_unrolled_workspace_bytes(int B, int Z, int H, int W,

@@ -58,7 +58,8 @@ class UnrolledParams(ctypes.Structure):
 
     _fields_ = [("rho", ctypes.c_float), ("lambda_", ctypes.c_float), ("gamma", ctypes.c_float),
                 ("iters", ctypes.c_int), ("tv_steps", ctypes.c_int), ("tv_tau", ctypes.c_float),
-                ("huber_eps", ctypes.c_float), ("ckpt_every", ctypes.c_int)]
+                ("huber_eps", ctypes.c_float), ("ckpt_every", ctypes.c_int),
+                ("keep_duals", ctypes.c_int)]
 
 
 class AdmmStats(ctypes.Structure):
@@ -452,7 +453,7 @@ class Batch:
 def _unrolled_params(rho, lam, gamma, cfg) -> UnrolledParams:
     return UnrolledParams(float(rho), float(lam), float(gamma), int(cfg["iters"]),
                           int(cfg["tv_steps"]), float(cfg["tv_tau"]), float(cfg["huber_eps"]),
-                          int(cfg["ckpt_every"]))
+                          int(cfg["ckpt_every"]), int(bool(cfg.get("keep_duals", False))))
 
 
 class _UnrolledADMM(torch.autograd.Function):
@@ -501,9 +502,12 @@ class _UnrolledADMM(torch.autograd.Function):
 
 def unrolled_admm(logits: torch.Tensor, b: torch.Tensor, rho: torch.Tensor, lam: torch.Tensor,
                   gamma: torch.Tensor, iters: int = 30, tv_steps: int = 20, tv_tau: float = 0.125,
-                  huber_eps: float = 1e-3, ckpt_every: int = 5) -> torch.Tensor:
+                  huber_eps: float = 1e-3, ckpt_every: int = 5,
+                  keep_duals: bool = False) -> torch.Tensor:
     """Differentiable v^K of the unrolled PnP-ADMM with relaxed masks sigmoid(logits)
-    [B,Z,H,W] and Huber-TV + z prior; b [B,H,W]; rho, lam, gamma 0-dim tensors."""
+    [B,Z,H,W] and Huber-TV + z prior; b [B,H,W]; rho, lam, gamma 0-dim tensors.
+    keep_duals: the backward keeps the dual iterates of a checkpoint segment
+    instead of recomputing them per slice (more device memory, same gradients)."""
     cfg = dict(iters=iters, tv_steps=tv_steps, tv_tau=tv_tau, huber_eps=huber_eps,
-               ckpt_every=ckpt_every)
+               ckpt_every=ckpt_every, keep_duals=keep_duals)
     return _UnrolledADMM.apply(logits, b, rho, lam, gamma, cfg)

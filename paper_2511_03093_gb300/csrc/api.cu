@@ -728,6 +728,7 @@ cslsm_status check_unrolled(int B, int Z, int H, int W, const cslsm_unrolled_par
     CHECK_ARG(std::isfinite(p->tv_tau) && p->tv_tau > 0.f && p->tv_tau <= 0.125f,
               "tv_tau must be in (0, 1/8]");
     CHECK_ARG(std::isfinite(p->huber_eps) && p->huber_eps >= 0.f, "huber_eps must be >= 0");
+    CHECK_ARG(p->keep_duals == 0 || p->keep_duals == 1, "keep_duals must be 0 or 1");
     return CSLSM_OK;
 }
 }  // namespace
@@ -735,7 +736,7 @@ cslsm_status check_unrolled(int B, int Z, int H, int W, const cslsm_unrolled_par
 size_t cslsm_unrolled_workspace_bytes(int B, int Z, int H, int W, const cslsm_unrolled_params *p)
 {
     if (check_unrolled(B, Z, H, W, p)) return 0;
-    return unrolled_workspace_bytes(B, Z, H, W, p->tv_steps, p->ckpt_every);
+    return unrolled_workspace_bytes(B, Z, H, W, p->tv_steps, p->ckpt_every, p->keep_duals);
 }
 
 cslsm_status cslsm_unrolled_forward(const float *logits, const float *b, int B, int Z, int H,
@@ -760,8 +761,8 @@ cslsm_status cslsm_unrolled_backward(const float *logits, const float *b, int B,
     CHECK_ARG(logits && b && ckpt && v_bar && logits_bar && scalar_bar && ws,
               "every pointer must be non-NULL");
     return unrolled_backward(B, Z, H, W, p->rho, p->lambda, p->gamma, p->iters, p->tv_steps,
-                             p->tv_tau, p->huber_eps, p->ckpt_every, logits, b, ckpt, v_bar,
-                             logits_bar, scalar_bar, ws, as_stream(stream));
+                             p->tv_tau, p->huber_eps, p->ckpt_every, p->keep_duals, logits, b,
+                             ckpt, v_bar, logits_bar, scalar_bar, ws, as_stream(stream));
 }
 
 cslsm_status cslsm_set_autotune(int mode)

@@ -226,14 +226,15 @@ struct BatchRun {
 };
 
 // ---- differentiable unrolled solver (kernels_diff.cu) -------------------------
-size_t unrolled_workspace_bytes(int B, int Z, int H, int W, int T, int S);
+size_t unrolled_workspace_bytes(int B, int Z, int H, int W, int T, int S, int keep);
 cslsm_status unrolled_forward(int B, int Z, int H, int W, float rho, float lam, float gam,
                               int K, int T, float tau, float eps, int S, const float *logits,
                               const float *b, float *vout, float *ckpt, void *ws, cudaStream_t s);
 cslsm_status unrolled_backward(int B, int Z, int H, int W, float rho, float lam, float gam,
-                               int K, int T, float tau, float eps, int S, const float *logits,
-                               const float *b, const float *ckpt, const float *vbar,
-                               float *logits_bar, double *scal_bar, void *ws, cudaStream_t s);
+                               int K, int T, float tau, float eps, int S, int keep,
+                               const float *logits, const float *b, const float *ckpt,
+                               const float *vbar, float *logits_bar, double *scal_bar, void *ws,
+                               cudaStream_t s);
 cslsm_status batch_build(const BatchSpec &spec, BatchRun &run);
 cslsm_status batch_set_wait(const BatchRun &run, double limit_s, int stall_test);
 // Enqueues the counter reset and the persistent launch (no state reset).

@@ -424,19 +424,26 @@ struct Ws {
     float *U, *D, *Wb, *Hb, *Pa, *Pb, *PH, *Useg, *Dseg;
     float *Ubar_new, *Ubar_old, *Wbar, *Dbar, *Hbar, *Pbar_a, *Pbar_b;
     double *acc;  // [3]: rho (direct), gamma (direct), theta (total)
+    // keep_duals: the prox inputs h and dual iterates p^0..p^T of every slice of
+    // a checkpoint segment, recorded by the segment's recompute:
+    // Hall [S][Z][B][H][W], PHall [S][Z][T + 1][B][2][H][W]; else null
+    float *Hall, *PHall;
 };
 
 inline size_t al(size_t x) { return (x + 255) & ~size_t(255); }
 
-size_t ws_bytes(const Geo &g, int T, int S)
+size_t ws_bytes(const Geo &g, int T, int S, int keep)
 {
     const size_t nv = (size_t)g.B * g.NV() * 4, hw = (size_t)g.B * g.HW() * 4;
-    return al(nv) * 3 + al(hw) + 2 * al(2 * hw) + al((size_t)(T + 1) * 2 * hw) +
-           2 * al((size_t)(S + 1) * nv) + al(nv) * 4 + al(hw) + 2 * al(2 * hw) +
-           al(3 * kAccCopies * sizeof(double));
+    size_t n = al(nv) * 3 + al(hw) + 2 * al(2 * hw) + al((size_t)(T + 1) * 2 * hw) +
+               2 * al((size_t)(S + 1) * nv) + al(nv) * 4 + al(hw) + 2 * al(2 * hw) +
+               al(3 * kAccCopies * sizeof(double));
+    if (keep)
+        n += al((size_t)S * g.Z * hw) + al((size_t)S * g.Z * (T + 1) * 2 * hw);
+    return n;
 }
 
-Ws carve(void *base, const Geo &g, int T, int S)
+Ws carve(void *base, const Geo &g, int T, int S, int keep)
 {
     const size_t nv = (size_t)g.B * g.NV() * 4, hw = (size_t)g.B * g.HW() * 4;
     char *p = (char *)base;
@@ -463,6 +470,8 @@ Ws carve(void *base, const Geo &g, int T, int S)
     w.Pbar_a = take(2 * hw);
     w.Pbar_b = take(2 * hw);
     w.acc = (double *)take(3 * kAccCopies * sizeof(double));
+    w.Hall = keep ? take((size_t)S * g.Z * hw) : nullptr;
+    w.PHall = keep ? take((size_t)S * g.Z * (T + 1) * 2 * hw) : nullptr;
     return w;
 }
 
@@ -515,9 +524,11 @@ cslsm_status slice_prox(const Geo &g, const Prm &P, const float *Hb, float *Pa, 
     return CSLSM_OK;
 }
 
-// One forward iteration on (U, D) in place; writes v when vout != null.
+// One forward iteration on (U, D) in place; writes v when vout != null.  With
+// Hrec / PHrec (keep_duals), slice n's prox input goes to Hrec + n [B][H][W]
+// and its dual iterates to PHrec + n [T + 1][B][2][H][W].
 cslsm_status fwd_iter(const Geo &g, const Prm &P, const float *logits, const float *b, Ws &w,
-                      float *vout, cudaStream_t s)
+                      float *vout, cudaStream_t s, float *Hrec = nullptr, float *PHrec = nullptr)
 {
     const float gam = g.Z > 1 ? P.gam : 0.f;
     LAUNCH(K_DIFF, ux_fwd_kernel<<<pgrid(g), kT, 0, s>>>(w.U, w.D, logits, b, g, P.rho, w.Wb, vout));
@@ -528,11 +539,14 @@ cslsm_status fwd_iter(const Geo &g, const Prm &P, const float *logits, const flo
         float *A, *C;
         neighbours(g, n, w.U, w.U, A, C);  // in place: the array holds the newest values
         const size_t off = (size_t)n * g.HW();
-        LAUNCH(K_DIFF, hform_kernel<<<pgrid(g), kT, 0, s>>>(w.Wb + off, A, C, g, P.rho, gam, w.Hb));
+        const size_t hwf = (size_t)g.B * g.HW();
+        float *Hb = Hrec ? Hrec + (size_t)n * hwf : w.Hb;
+        float *PH = PHrec ? PHrec + (size_t)n * (P.T + 1) * 2 * hwf : nullptr;
+        LAUNCH(K_DIFF, hform_kernel<<<pgrid(g), kT, 0, s>>>(w.Wb + off, A, C, g, P.rho, gam, Hb));
         float *pT = nullptr;
-        cslsm_status e = slice_prox(g, Q, w.Hb, w.Pa, w.Pb, nullptr, &pT, s);
+        cslsm_status e = slice_prox(g, Q, Hb, w.Pa, w.Pb, PH, &pT, s);
         if (e) return e;
-        LAUNCH(K_DIFF, prox_out_kernel<<<pgrid(g), kT, 0, s>>>(pT, w.Hb, g, theta, w.Wb + off,
+        LAUNCH(K_DIFF, prox_out_kernel<<<pgrid(g), kT, 0, s>>>(pT, Hb, g, theta, w.Wb + off,
                                                                  w.U + off, w.D + off));
     }
     return CSLSM_OK;
@@ -540,9 +554,9 @@ cslsm_status fwd_iter(const Geo &g, const Prm &P, const float *logits, const flo
 
 }  // namespace
 
-size_t unrolled_workspace_bytes(int B, int Z, int H, int W, int T, int S)
+size_t unrolled_workspace_bytes(int B, int Z, int H, int W, int T, int S, int keep)
 {
-    return ws_bytes(Geo{B, Z, H, W}, T, S);
+    return ws_bytes(Geo{B, Z, H, W}, T, S, keep);
 }
 
 cslsm_status unrolled_forward(int B, int Z, int H, int W, float rho, float lam, float gam,
@@ -551,7 +565,7 @@ cslsm_status unrolled_forward(int B, int Z, int H, int W, float rho, float lam, 
 {
     const Geo g{B, Z, H, W};
     const Prm P{rho, lam, gam, tau, eps, K, T, S};
-    Ws w = carve(ws, g, T, S);
+    Ws w = carve(ws, g, T, S, 0);  // the kept duals, if any, lie beyond this part
     const size_t nv = (size_t)B * g.NV();
     CSLSM_CUDA(cudaMemsetAsync(w.U, 0, nv * 4, s));
     CSLSM_CUDA(cudaMemsetAsync(w.D, 0, nv * 4, s));
@@ -568,16 +582,18 @@ cslsm_status unrolled_forward(int B, int Z, int H, int W, float rho, float lam, 
 }
 
 cslsm_status unrolled_backward(int B, int Z, int H, int W, float rho, float lam, float gam,
-                               int K, int T, float tau, float eps, int S, const float *logits,
-                               const float *b, const float *ckpt, const float *vbar,
-                               float *logits_bar, double *scal_bar, void *ws, cudaStream_t s)
+                               int K, int T, float tau, float eps, int S, int keep,
+                               const float *logits, const float *b, const float *ckpt,
+                               const float *vbar, float *logits_bar, double *scal_bar, void *ws,
+                               cudaStream_t s)
 {
     const Geo g{B, Z, H, W};
     Prm P{rho, lam, gam, tau, eps, K, T, S};
     const float gz = Z > 1 ? gam : 0.f;
     P.gam = gz;
-    Ws w = carve(ws, g, T, S);
+    Ws w = carve(ws, g, T, S, keep);
     const size_t nv = (size_t)B * g.NV(), HW = g.HW(), hw2 = (size_t)B * 2 * HW;
+    const size_t hwf = (size_t)B * HW;
     const float den = rho + 2.f * gz, theta = lam / den;
     CSLSM_CUDA(cudaMemsetAsync(w.acc, 0, 3 * kAccCopies * sizeof(double), s));
     CSLSM_CUDA(cudaMemsetAsync(logits_bar, 0, nv * 4, s));
@@ -598,7 +614,11 @@ cslsm_status unrolled_backward(int B, int Z, int H, int W, float rho, float lam,
             CSLSM_CUDA(cudaMemcpyAsync(w.Dseg + (size_t)slot * nv, w.D, nv * 4,
                                        cudaMemcpyDeviceToDevice, s));
             if (k < k1) {
-                cslsm_status e = fwd_iter(g, P, logits, b, w, nullptr, s);
+                // keep_duals: record every slice's h and dual iterates of iteration k
+                cslsm_status e =
+                    fwd_iter(g, P, logits, b, w, nullptr, s,
+                             keep ? w.Hall + (size_t)slot * Z * hwf : nullptr,
+                             keep ? w.PHall + (size_t)slot * Z * (T + 1) * hw2 : nullptr);
                 if (e) return e;
             }
         }
@@ -620,18 +640,26 @@ cslsm_status unrolled_backward(int B, int Z, int H, int W, float rho, float lam,
                 float *Ab, *Cb;
                 neighbours(g, n, w.Ubar_old, w.Ubar_new, Ab, Cb);
                 const size_t off = (size_t)n * HW;
-                LAUNCH(K_DIFF, hform_kernel<<<pgrid(g), kT, 0, s>>>(w.Wb + off, A, C, g, rho, gz,
-                                                                    w.Hb));
-                float *pT = nullptr;
-                cslsm_status e = slice_prox(g, P, w.Hb, w.Pa, w.Pb, w.PH, &pT, s);
-                if (e) return e;
+                const int Tn = theta > 0.f ? T : 0;
+                // the prox input h and its dual iterates p^0 .. p^T: kept by the
+                // segment's recompute, or recomputed here
+                float *Hn = w.Hb, *PHn = w.PH, *pT = nullptr;
+                if (keep) {
+                    Hn = w.Hall + ((size_t)slot * Z + n) * hwf;
+                    PHn = w.PHall + ((size_t)slot * Z + n) * (T + 1) * hw2;
+                    pT = PHn + (size_t)Tn * hw2;
+                } else {
+                    LAUNCH(K_DIFF, hform_kernel<<<pgrid(g), kT, 0, s>>>(w.Wb + off, A, C, g, rho,
+                                                                        gz, w.Hb));
+                    cslsm_status e = slice_prox(g, P, w.Hb, w.Pa, w.Pb, w.PH, &pT, s);
+                    if (e) return e;
+                }
                 LAUNCH(K_DIFF, prox_out_bwd_kernel<<<pgrid(g), kT, 0, s>>>(
                                    pT, g, theta, w.Ubar_new + off, w.Hbar, w.Pbar_a, w.acc));
-                const int Tn = theta > 0.f ? T : 0;
                 float *pb_in = w.Pbar_a, *pb_out = w.Pbar_b;
                 const dim3 tgrid((unsigned)(((W + kBT - 1) / kBT) * ((H + kBT - 1) / kBT)), B);
                 for (int t = Tn - 1; t >= 0; --t) {
-                    DualArgs Ad{w.PH + (size_t)t * hw2, nullptr, w.Hb, g, 1.f / theta, tau,
+                    DualArgs Ad{PHn + (size_t)t * hw2, nullptr, Hn, g, 1.f / theta, tau,
                                 eps / theta};
                     LAUNCH(K_DIFF, dual_bwd_kernel<<<tgrid, kT, 0, s>>>(Ad, pb_in, pb_out, w.Hbar,
                                                                          eps, w.acc));

@@ -39,7 +39,7 @@ def test_library_exports_every_declared_symbol(L):
 
 
 def test_status_strings_and_version(L):
-    assert L.cslsm_abi_version() == 3
+    assert L.cslsm_abi_version() == 4
     for code, name in [(0, b"CSLSM_OK"), (1, b"CSLSM_ERR_INVALID_ARG"), (2, b"CSLSM_ERR_CUDA"),
                        (3, b"CSLSM_ERR_TIMEOUT"), (4, b"CSLSM_ERR_UNSUPPORTED"),
                        (5, b"CSLSM_ERR_OOM")]:

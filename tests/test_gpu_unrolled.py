@@ -75,6 +75,26 @@ def test_checkpoint_period_does_not_change_gradients(cs):
         assert o[1:] == out[0][1:]
 
 
+@pytest.mark.parametrize("B,Z,H,W,every", [(1, 4, 20, 18, 3), (2, 3, 37, 29, 1), (1, 2, 30, 33, 4)])
+def test_kept_duals_give_the_same_gradients(cs, B, Z, H, W, every):
+    """keep_duals reads the dual iterates the segment recompute stored instead of
+    recomputing them per slice: the gradients must not change by a bit."""
+    logits, b, _ = _problem(9 + H, B, Z, H, W)
+    vbar = torch.randn(B, Z, H, W, generator=torch.Generator().manual_seed(7)).cuda()
+    out = []
+    for keep in (False, True):
+        lg = logits.cuda().requires_grad_(True)
+        r, l_, gm = _scalars()
+        v = cs.unrolled_admm(lg, b.cuda(), r, l_, gm,
+                             **dict(CFG, ckpt_every=every, keep_duals=keep))
+        (v * vbar).sum().backward()
+        out.append((v.detach().cpu().numpy(), lg.grad.cpu().numpy(), float(r.grad),
+                    float(l_.grad), float(gm.grad)))
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][1], out[1][1])
+    assert out[0][2:] == out[1][2:]
+
+
 def test_finite_differences_on_gpu(cs):
     """Central differences with 1e-4 relative perturbations of rho, lambda, gamma."""
     logits, b, x = _problem(8, 1, 4, 32, 28)
@@ -101,8 +121,9 @@ def test_finite_differences_on_gpu(cs):
 
 
 def test_full_size_batch8(cs):
-    """Batch 8 of 512 x 512 x 16, 30 iterations, checkpoint every 5: finite gradients
-    and a directional finite-difference check along lambda."""
+    """Batch 8 of 512 x 512 x 16, 30 iterations, checkpoint every 5: finite gradients,
+    a directional finite-difference check along lambda, and the same gradients with
+    the dual iterates kept."""
     B, Z, H, W = 8, 16, 512, 512
     g = torch.Generator(device="cuda").manual_seed(11)
     logits = torch.randn(B, Z, H, W, generator=g, device="cuda")
@@ -122,3 +143,10 @@ def test_full_size_batch8(cs):
         lm = 0.5 * ((cs.unrolled_admm(logits, b, *_scalars(1.0, 0.05 - h, 0.2), **cfg) - x) ** 2).mean()
     fd = (float(lp) - float(lm)) / (2 * h)
     assert abs(fd - float(l_.grad)) <= 5e-2 * max(abs(float(l_.grad)), 1e-6), (fd, float(l_.grad))
+    # the same gradients with the dual iterates kept (about 29 GB of workspace)
+    lg2 = logits.clone().requires_grad_(True)
+    r2, l2, g2 = _scalars(1.0, 0.05, 0.2)
+    v2 = cs.unrolled_admm(lg2, b, r2, l2, g2, **dict(cfg, keep_duals=True))
+    (0.5 * ((v2 - x) ** 2).mean()).backward()
+    assert torch.equal(lg2.grad, lg.grad)
+    assert [float(t.grad) for t in (r2, l2, g2)] == [float(t.grad) for t in (r, l_, gm)]
