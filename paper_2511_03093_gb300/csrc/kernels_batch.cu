@@ -8,7 +8,7 @@
 // tile of one slice for one phase: it forms g on its region (the tile plus a
 // halo of k + 1 pixels; with gamma > 0 from the newest u_{n-1} and the previous
 // u_{n+1}, Sec. III-C), loads the dual field p that the previous phase left in
-// the item's L2-resident exchange buffer (p = 0 in the first phase), runs the
+// the item's exchange buffer (p = 0 in the first phase), runs the
 // steps with the dual field of every warp's rows in registers, and stores p of
 // its own tile for the next phase, or, in the last phase, u = g - theta div p
 // and d = w - u.  With gamma > 0 the slices follow one another in
@@ -22,8 +22,9 @@
 //
 // Scheduling.  The grid is exactly as many CTAs as fit on the GPU at once.
 // Each CTA takes the next unit number from a global ticket counter, waits
-// until the item's completed-unit counter reaches the count the unit depends
-// on, runs the unit and increments the counter.  Because units are taken in
+// until the item's completed-unit counter (read with acquire semantics)
+// reaches the count the unit depends on, runs the unit and increments the
+// counter with release semantics after a CTA barrier.  Because units are taken in
 // global order and every CTA is resident, the units waited for are already
 // held by running CTAs: the schedule cannot deadlock.  Every wait is bounded
 // (a wall-clock limit read from %globaltimer); on expiry the CTA raises the
