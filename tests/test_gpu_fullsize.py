@@ -1,0 +1,67 @@
+"""Parity at the full size of the 1024 x 1024 x 32 configuration (Bernoulli(0.5)
+patterns, Poisson peak 200 + Gaussian 0.01), in the launch configurations the
+benchmark's secondary workloads time: one whole ADMM iteration with the Tikhonov
+prior and with the TV prior (gamma = 0) against the FP64 oracle's iteration, and
+the BM3D match lists of one full 1024 x 1024 slice, bit for bit.  The smaller
+parity tests cover ragged shapes; these cover the sizes where tiles, grids and
+reductions run at their largest."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.gpu_util import REL_ITER, rel_l2, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cs():
+    import torch
+
+    from paper_2511_03093_gb300 import build as b
+
+    b.build()
+    import paper_2511_03093_gb300 as m
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return m
+
+
+@pytest.fixture(scope="module")
+def cfg3():
+    wk = synth.WORKLOADS["bm3d_1024x1024x32"]
+    return wk, synth.generate(wk)
+
+
+@pytest.mark.parametrize("den", ["tikhonov", "tv"])
+def test_one_iteration_full_size(cs, cfg3, den):
+    """One GPU iteration from u = d = 0 (x-update, the prior's u-step over all 32
+    slices, dual update) against the oracle's first iteration."""
+    import torch
+
+    wk, data = cfg3
+    kw = dict(rho=1.0, lam=0.05, gamma=0.0, denoiser=den, tv_inner=20)
+    v_r, u_r, d_r, _ = oracle.admm(data["b64"], data["masks"], wk.Z, iters=1, **kw)
+    plan = cs.Plan(wk.H, wk.W, 1, wk.Z, to_dev(data["masks"]))
+    zeros = np.zeros((wk.Z, wk.H, wk.W), dtype=np.float32)
+    u, d = to_dev(zeros), to_dev(zeros)
+    v = plan.solve(to_dev(data["b"]), cs.Params(iters=1, **kw), u=u, d=d, init_user=True)
+    torch.cuda.synchronize()
+    assert rel_l2(to_np(v), v_r) <= REL_ITER
+    assert rel_l2(to_np(u), u_r) <= REL_ITER
+    assert rel_l2(to_np(d), d_r) <= REL_ITER
+    plan.close()
+
+
+def test_bm3d_match_full_slice(cs, cfg3):
+    """Hard-stage block matching of one full 1024 x 1024 slice of noisy data (115,600
+    references): lists and counts equal the oracle's exactly."""
+    wk, data = cfg3
+    rng = np.random.default_rng(1003)
+    img = np.clip(data["x"][5] + 0.05 * rng.standard_normal((wk.H, wk.W)), -0.2, 1.2)
+    img = img.astype(np.float32)[None]
+    lists, counts = cs.bm3d_match(to_dev(img), 1)
+    idx, cnt = oracle.bm3d_match(img[0], 1)
+    np.testing.assert_array_equal(counts.cpu().numpy()[0], cnt)
+    np.testing.assert_array_equal(lists.cpu().numpy()[0], idx)
