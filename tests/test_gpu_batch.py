@@ -66,6 +66,36 @@ def test_batch_equals_per_volume(cs, gamma, storage, T):
     batch.close()
 
 
+@pytest.mark.parametrize("storage", ["fp32", "bf16"])
+def test_batch_equals_per_volume_benchmark_sizes(cs, storage):
+    """Items of the 64-measurement benchmark's size distribution, including its
+    largest (1024 x 1024 x 32), TV + z, 3 iterations: bit-identical to the plain
+    per-volume solves."""
+    import torch
+
+    sizes = [(32, 1024, 1024), (8, 256, 256), (16, 768, 768)]
+    items = []
+    for k, (Z, S, _) in enumerate(sizes):
+        w = synth.Workload(f"bb{k}", Z, S, S, drift=True, mask_p=0.3, peak=50.0, sigma_g=0.02,
+                           seed=4100 + k, n_blobs=min(2000, synth.blob_count(Z, S, S)))
+        data = synth.generate(w)
+        plan = cs.Plan(S, S, 1, Z, to_dev(data["masks"]))
+        items.append((plan, to_dev(data["b"]),
+                      torch.empty((Z, S, S), dtype=torch.float32, device="cuda")))
+    prm = cs.Params(rho=1.0, lam=0.05, gamma=0.2, iters=3, denoiser="tv", tv_inner=20,
+                    storage=storage)
+    batch = cs.Batch(items, prm)
+    batch.run()
+    batch.wait()
+    for plan, b, v in items:
+        ref = plan.solve(b, prm)
+        torch.cuda.synchronize()
+        assert torch.equal(v, ref)
+    batch.close()
+    for plan, _, _ in items:
+        plan.close()
+
+
 def test_batch_autotuned_tiles(cs):
     import torch
 
