@@ -4,7 +4,8 @@ benchmark's secondary workloads time: one whole ADMM iteration with the Tikhonov
 prior and with the TV prior (gamma = 0) against the FP64 oracle's iteration, and
 the BM3D match lists of one full 1024 x 1024 slice, bit for bit.  The smaller
 parity tests cover ragged shapes; these cover the sizes where tiles, grids and
-reductions run at their largest."""
+reductions run at their largest.  Both BM3D stages are also checked on one full
+1024 x 1024 slice."""
 import numpy as np
 import pytest
 
@@ -65,3 +66,22 @@ def test_bm3d_match_full_slice(cs, cfg3):
     idx, cnt = oracle.bm3d_match(img[0], 1)
     np.testing.assert_array_equal(counts.cpu().numpy()[0], cnt)
     np.testing.assert_array_equal(lists.cpu().numpy()[0], idx)
+
+
+def test_bm3d_stages_full_slice(cs):
+    """Both BM3D stages on one full 1024 x 1024 slice of noisy data (sigma 0.05):
+    the Wiener stage on the oracle's basic estimate within relative L2 1e-5; the
+    hard stage, whose threshold can flip on 1-ulp differences between FP32 and FP64
+    coefficients, within 1e-4 with at most 0.1 % of pixels off by more than 1e-4."""
+    w = synth.Workload("s", 1, 1024, 1024, seed=1003, peak=None,
+                       n_blobs=synth.blob_count(1, 1024, 1024))
+    x = synth.generate(w)["x"][0]
+    img = (x + 0.05 * np.random.default_rng(3).standard_normal(x.shape)).astype(np.float32)
+    basic_r = oracle.bm3d_stage(img, 0.05)
+    basic = to_np(cs.bm3d_stage(1, to_dev(img[None]), 0.05))[0]
+    assert rel_l2(basic, basic_r) <= 1e-4
+    assert np.mean(np.abs(basic - basic_r) > 1e-4) <= 1e-3
+    guide = basic_r.astype(np.float32)
+    wien_r = oracle.bm3d_stage(img, 0.05, guide=guide)
+    wien = to_np(cs.bm3d_stage(2, to_dev(img[None]), 0.05, guide=to_dev(guide[None])))[0]
+    assert rel_l2(wien, wien_r) <= REL_ITER
