@@ -87,6 +87,46 @@ def test_invalid_arguments_rejected_on_host(L):
     assert L.cslsm_plan_destroy(None) == 0
 
 
+def test_newer_entry_points_reject_bad_arguments_on_host(L):
+    """3-D SSIM, the batch, the unrolled solver and the allocation-free BM3D refuse
+    empty, oversized or inconsistent arguments before any GPU work."""
+    import paper_2511_03093_gb300 as cs
+
+    fake = ctypes.c_void_p(0x1000)  # never dereferenced
+    INVALID = 1
+    for Z, H, W in ((0, 8, 8), (4, 0, 8), (4, 8, -1), (1 << 11, 1 << 10, 1 << 10)):
+        assert L.cslsm_ssim3d(fake, fake, Z, H, W, fake, None) == INVALID, (Z, H, W)
+    assert L.cslsm_ssim3d(None, fake, 4, 8, 8, fake, None) == INVALID
+    b = ctypes.c_void_p()
+    p = _params()
+    assert L.cslsm_batch_create(ctypes.byref(b), None, 0, ctypes.byref(p), None) == INVALID
+    assert b"at least one item" in L.cslsm_last_error()
+    # unrolled solver parameters: the workspace query returns 0 for invalid ones
+    good = dict(rho=1.0, lam=0.05, gamma=0.2, cfg=dict(iters=4, tv_steps=8, tv_tau=0.125,
+                                                       huber_eps=1e-3, ckpt_every=2))
+    up = cs._unrolled_params(good["rho"], good["lam"], good["gamma"], good["cfg"])
+    assert L.cslsm_unrolled_workspace_bytes(1, 4, 16, 16, ctypes.byref(up)) > 0
+    for field, value in (("keep_duals", 2), ("tv_tau", 0.2), ("iters", 0), ("ckpt_every", 0),
+                         ("rho", 0.0), ("lambda_", -1.0), ("huber_eps", -1.0)):
+        bad = cs._unrolled_params(good["rho"], good["lam"], good["gamma"], good["cfg"])
+        setattr(bad, field, value)
+        assert L.cslsm_unrolled_workspace_bytes(1, 4, 16, 16, ctypes.byref(bad)) == 0, field
+    assert L.cslsm_unrolled_workspace_bytes(0, 4, 16, 16, ctypes.byref(up)) == 0
+    # keep_duals grows the workspace by ckpt_every x Z x (2 tv_steps + 3) x B H W floats
+    kp = cs._unrolled_params(1.0, 0.05, 0.2, dict(good["cfg"], keep_duals=True))
+    grow = L.cslsm_unrolled_workspace_bytes(1, 4, 16, 16, ctypes.byref(kp)) - \
+        L.cslsm_unrolled_workspace_bytes(1, 4, 16, 16, ctypes.byref(up))
+    assert 2 * 4 * (2 * 8 + 3) * 16 * 16 * 4 <= grow <= 2 * 4 * (2 * 8 + 3) * 16 * 16 * 4 + 512
+    # the allocation-free BM3D: bad sizes and sigma, overlap
+    assert L.cslsm_denoise_bm3d_noalloc(fake, ctypes.c_void_p(0x10000000), 0, 8, 8,
+                                        ctypes.c_float(0.05), None) == INVALID
+    assert L.cslsm_denoise_bm3d_noalloc(fake, ctypes.c_void_p(0x10000000), 1, 8, 8,
+                                        ctypes.c_float(0.0), None) == INVALID
+    assert L.cslsm_denoise_bm3d_noalloc(fake, ctypes.c_void_p(0x1004), 1, 8, 8,
+                                        ctypes.c_float(0.05), None) == INVALID
+    assert b"overlap" in L.cslsm_last_error()
+
+
 def test_binding_refuses_cpu_tensors():
     import torch
 
