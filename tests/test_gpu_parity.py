@@ -132,6 +132,16 @@ ITER_CASES = [
     ("tv", 0.2, (3, 4, 29, 64, False)),
     ("tv", 0.4, (1, 2, 36, 30, True)),
     ("tv", 0.2, (1, 16, 70, 66, True)),
+    # degenerate geometries: one slice with gamma > 0 (no z term), a single pixel,
+    # single-row and single-column slices, two one-plane shots (the cyclic z
+    # neighbours of each slice are the same slice)
+    ("tv", 0.2, (1, 1, 37, 53, True)),
+    ("tikhonov", 0.3, (1, 1, 5, 5, True)),
+    ("tv", 0.0, (1, 1, 1, 1, True)),
+    ("tv", 0.2, (1, 3, 1, 70, True)),
+    ("tv", 0.2, (1, 3, 70, 1, True)),
+    ("tv", 0.2, (2, 1, 17, 19, True)),
+    ("tikhonov", 0.3, (2, 1, 17, 19, True)),
 ]
 
 
@@ -155,6 +165,31 @@ def test_one_iteration_from_state(cs, den, gamma, geom):
     torch.cuda.synchronize()
     v_r, u_r, d_r, _ = oracle.admm(b, masks, Z, rho=0.8, lam=0.07, gamma=gamma, iters=1,
                                    denoiser=den, tv_inner=20, u0=u0, d0=d0)
+    assert rel_l2(to_np(v), v_r) <= REL_ITER
+    assert rel_l2(to_np(u), u_r) <= REL_ITER
+    assert rel_l2(to_np(d), d_r) <= REL_ITER
+    plan.close()
+
+
+@pytest.mark.parametrize("T", [1, 2, 3])
+def test_one_iteration_few_tv_steps(cs, T):
+    """The TV + z u-step with one to three Chambolle steps (a phase shorter than the
+    halo logic's usual k) against the oracle."""
+    import torch
+
+    N, R, H, W = 1, 6, 45, 77
+    rng = np.random.default_rng(20 + T)
+    masks = (rng.random((R, H, W)) < 0.5).astype(np.uint8)
+    b = (rng.random((N, H, W)) * 3).astype(np.float32)
+    u0 = rng.random((R, H, W)).astype(np.float32)
+    d0 = (0.1 * rng.standard_normal((R, H, W))).astype(np.float32)
+    prm = cs.Params(rho=0.8, lam=0.07, gamma=0.2, iters=1, denoiser="tv", tv_inner=T)
+    plan = cs.Plan(H, W, N, R, to_dev(masks))
+    u, d = to_dev(u0), to_dev(d0)
+    v = plan.solve(to_dev(b), prm, u=u, d=d, init_user=True)
+    torch.cuda.synchronize()
+    v_r, u_r, d_r, _ = oracle.admm(b, masks, R, rho=0.8, lam=0.07, gamma=0.2, iters=1,
+                                   denoiser="tv", tv_inner=T, u0=u0, d0=d0)
     assert rel_l2(to_np(v), v_r) <= REL_ITER
     assert rel_l2(to_np(u), u_r) <= REL_ITER
     assert rel_l2(to_np(d), d_r) <= REL_ITER
