@@ -171,6 +171,32 @@ def test_one_iteration_from_state(cs, den, gamma, geom):
     plan.close()
 
 
+@pytest.mark.parametrize("fill", [0, 1])
+@pytest.mark.parametrize("den", ["tv", "tikhonov"])
+def test_one_iteration_constant_patterns(cs, fill, den):
+    """Every DMD pattern closed (D = 0: the x-update keeps g) or open (D = R)."""
+    import torch
+
+    N, R, H, W = 1, 5, 33, 41
+    rng = np.random.default_rng(30 + fill)
+    masks = np.full((R, H, W), fill, dtype=np.uint8)
+    b = (rng.random((N, H, W)) * 3).astype(np.float32)
+    u0 = rng.random((R, H, W)).astype(np.float32)
+    d0 = (0.1 * rng.standard_normal((R, H, W))).astype(np.float32)
+    kw = dict(rho=0.8, lam=0.07, gamma=0.2, iters=1, denoiser=den, tv_inner=20)
+    plan = cs.Plan(H, W, N, R, to_dev(masks))
+    u, d = to_dev(u0), to_dev(d0)
+    v = plan.solve(to_dev(b), cs.Params(**kw), u=u, d=d, init_user=True)
+    torch.cuda.synchronize()
+    v_r, u_r, d_r, _ = oracle.admm(b, masks, R, u0=u0, d0=d0, **kw)
+    assert rel_l2(to_np(v), v_r) <= REL_ITER
+    assert rel_l2(to_np(u), u_r) <= REL_ITER
+    assert rel_l2(to_np(d), d_r) <= REL_ITER
+    if fill == 0:  # nothing measured: v = u - d exactly
+        np.testing.assert_array_equal(to_np(v), u0 - d0)
+    plan.close()
+
+
 @pytest.mark.parametrize("T", [1, 2, 3])
 def test_one_iteration_few_tv_steps(cs, T):
     """The TV + z u-step with one to three Chambolle steps (a phase shorter than the
