@@ -114,7 +114,7 @@ def _quality(cs, v, data, dev):
 class ClockSampler:
     """nvidia-smi clock / throttle samples while the timed region runs."""
 
-    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -124,7 +124,7 @@ class ClockSampler:
         out_dir = os.environ.get("BENCH_CLOCKS_DIR") or tempfile.gettempdir()
         self.path = os.path.join(out_dir, f"cslsm_clocks_{os.getpid()}.csv")
         cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-               "-lms", "100"]
+               "-lms", "50"]
         if gpu_id:
             cmd += ["-i", gpu_id]
         try:
@@ -133,6 +133,10 @@ class ClockSampler:
             self.proc = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
+
+    def window(self, t0: float, t1: float) -> None:
+        """Host wall-clock bounds (time.time()) of the timed region."""
+        self.t0, self.t1 = t0, t1
 
     def stop(self):
         if self.proc is None:
@@ -143,23 +147,39 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.f.close()
-        rows = []
-        for line in open(self.path):
-            parts = [x.strip() for x in line.split(",")]
-            if len(parts) < 8:
-                continue
-            try:
-                rows.append((float(parts[0]), float(parts[1]), parts[4:8]))
-            except ValueError:
-                continue
-        if not rows:
-            return None
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for _, _, r in rows for i, x in enumerate(r)
-                          if x.lower() == "active"})
-        loaded = [s for s, _, _ in rows]
-        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(m for _, m, _ in rows),
-                "reasons": reasons, "samples": len(rows)}
+        return summarize_clocks(open(self.path).read().splitlines(),
+                                getattr(self, "t0", None), getattr(self, "t1", None))
+
+
+def summarize_clocks(lines, t0=None, t1=None):
+    """Median SM clock, max clock and the throttle reasons seen, over the samples
+    taken inside [t0, t1] (host wall clock; every sample if none falls inside)."""
+    import datetime
+
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    rows = []
+    for line in lines:
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) < 9:
+            continue
+        try:
+            sm, sm_max = float(parts[1]), float(parts[2])
+        except ValueError:
+            continue
+        try:
+            ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            ts = None  # unknown timestamp format: the sample still counts overall
+        rows.append((ts, sm, sm_max, parts[5:9]))
+    if not rows:
+        return None
+    inside = [r for r in rows if t0 is not None and r[0] is not None and t0 <= r[0] <= t1]
+    use = inside or rows
+    reasons = sorted({names[i] for _, _, _, r in use for i, x in enumerate(r)
+                      if x.lower() == "active"})
+    return {"sm_mhz": statistics.median(s for _, s, _, _ in use),
+            "sm_max_mhz": max(m for _, _, m, _ in use), "reasons": reasons,
+            "samples": len(use), "samples_in_timed_region": len(inside)}
 
 
 def rank_workload(rank: int):
@@ -283,10 +303,6 @@ def run_ours(args) -> None:
         if world > 1:
             dist.barrier()
 
-    for _ in range(max(args.warmup, 0)):
-        step()
-    torch.cuda.synchronize()
-
     gpu_id = None
     try:
         gpu_id = str(torch.cuda.get_device_properties(dev).uuid)
@@ -294,13 +310,20 @@ def run_ours(args) -> None:
             gpu_id = "GPU-" + gpu_id
     except Exception:
         gpu_id = None
+    # the sampler starts before the warm-up so that it is running when the timed
+    # region begins; only the samples inside the region are summarised
+    clocks = ClockSampler(gpu_id) if rank == 0 else None
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+
     ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     cs.timing_read(DOMINANT, reset=True)
-    clocks = ClockSampler(gpu_id) if rank == 0 else None
 
     barrier()
     torch.cuda.synchronize()
+    t_wall0 = time.time()
     n0 = cs.launch_count()
     cs.timing_enable(TIMING_PERIOD)
     for k in range(args.steps):
@@ -309,9 +332,12 @@ def run_ours(args) -> None:
         step()
         ev_e[k].record(stream)
     torch.cuda.synchronize()
+    t_wall1 = time.time()
     barrier()
     cs.timing_enable(0)
     launches = cs.launch_count() - n0
+    if clocks:
+        clocks.window(t_wall0, t_wall1)
     clk = clocks.stop() if clocks else None
     step_ms = [ev_s[k].elapsed_time(ev_e[k]) for k in range(args.steps)]
     total_ms = sum(step_ms)

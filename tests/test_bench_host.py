@@ -1,0 +1,41 @@
+"""Host-side logic of bench.py that needs no GPU: the clock-sample summary and the
+streaming byte model of the TV path."""
+import datetime
+import time
+
+import bench
+
+
+def _line(t, clk, reasons=("Not Active",) * 4, stamp=None):
+    ts = stamp or datetime.datetime.fromtimestamp(t).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]
+    return ", ".join([ts, str(clk), "2070", "900.0", "0x0"] + list(reasons))
+
+
+def test_clock_summary_keeps_the_timed_region():
+    now = time.time()
+    lines = ["", "garbage",
+             _line(now - 1.0, 990),  # idle, before the timed region
+             _line(now + 0.01, 2070),
+             _line(now + 0.06, 2070, ("Not Active", "Not Active", "Not Active", "Active")),
+             _line(now + 0.11, 2055),
+             _line(now + 2.0, 1000)]  # after it
+    s = bench.summarize_clocks(lines, now, now + 0.2)
+    assert s["samples_in_timed_region"] == 3 and s["samples"] == 3
+    assert s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["sw_power_cap"]
+
+
+def test_clock_summary_falls_back_to_every_sample():
+    now = time.time()
+    lines = [_line(now, 2000, stamp="not a time"), _line(now, 2070, stamp="??"),
+             _line(now, 1900, ("Active", "Not Active", "Not Active", "Not Active"))]
+    s = bench.summarize_clocks(lines, now + 10, now + 11)
+    assert s["samples_in_timed_region"] == 0 and s["samples"] == 3
+    assert s["sm_mhz"] == 2000.0 and s["reasons"] == ["hw_slowdown"]
+    assert bench.summarize_clocks(["x, y"], now, now) is None
+
+
+def test_streaming_byte_model():
+    # x-update 12.125 + 4 / R, first pass 12, 19 later passes of 20, finalize 20, z term 8
+    assert bench.tv_stream_bytes(16, 20, True) == 12.125 + 0.25 + 12 + 19 * 20 + 20 + 8
+    assert bench.tv_stream_bytes(32, 20, False) == 424.25
