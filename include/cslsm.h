@@ -301,7 +301,9 @@ cslsm_status cslsm_unrolled_backward(const float *logits, const float *b, int B,
  * (64 MiB) on every GPU that loads the library, until the process exits.  A
  * call whose scratch (cslsm_bm3d_scratch_bytes(Z, H, W): about 33 bytes per
  * voxel, e.g. 8.5 MB for one 512 x 512 slice) exceeds it returns
- * CSLSM_ERR_INVALID_ARG before any GPU work.
+ * CSLSM_ERR_INVALID_ARG before any GPU work, and so does a call whose in or
+ * out is not device (or managed) memory of the current device (the array
+ * used is the current device's).
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current.  Every call on a device
  * shares the one array and clears the part it uses at its start, so calls

@@ -406,10 +406,11 @@ def denoise_bm3d_noalloc(x: torch.Tensor, sigma: float, out: torch.Tensor | None
     Z, H, W = x.shape
     if out is None:
         out = torch.empty_like(x)
-    _check(lib().cslsm_denoise_bm3d_noalloc(_dev(x, "x", torch.float32),
-                                            _dev(out, "out", torch.float32, (Z, H, W)), Z, H, W,
-                                            float(sigma), _stream(stream)),
-           "cslsm_denoise_bm3d_noalloc")
+    with torch.cuda.device(x.device):  # the scratch array used is the current device's
+        _check(lib().cslsm_denoise_bm3d_noalloc(_dev(x, "x", torch.float32),
+                                                _dev(out, "out", torch.float32, (Z, H, W)), Z,
+                                                H, W, float(sigma), _stream(stream)),
+               "cslsm_denoise_bm3d_noalloc")
     return out
 
 

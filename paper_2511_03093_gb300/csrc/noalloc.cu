@@ -50,6 +50,29 @@ cslsm_status scratch_address(void **out)
     return CSLSM_OK;
 }
 
+// The scratch address is per device, so in and out must be device (or
+// managed) memory of the device that is current: a buffer of another GPU, or
+// host memory, would otherwise reach this device's kernels.
+cslsm_status check_device_buffer(const void *p, const char *name)
+{
+    int dev = 0;
+    CSLSM_CUDA(cudaGetDevice(&dev));
+    cudaPointerAttributes at{};
+    const cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("%s: cudaPointerGetAttributes failed: %s", name, cudaGetErrorString(e));
+        return CSLSM_ERR_INVALID_ARG;
+    }
+    const bool device_mem = at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (!device_mem || at.device != dev) {
+        set_error("%s must be device memory of the current device %d (memory type %d, device %d)",
+                  name, dev, (int)at.type, at.device);
+        return CSLSM_ERR_INVALID_ARG;
+    }
+    return CSLSM_OK;
+}
+
 }  // namespace
 }  // namespace cslsm
 
@@ -93,8 +116,11 @@ cslsm_status cslsm_denoise_bm3d_noalloc(const float *in, float *out, int Z, int 
                   Z, H, W, need, kScratchBytes);
         return CSLSM_ERR_INVALID_ARG;
     }
+    cslsm_status st = check_device_buffer(in, "in");
+    if (st) return st;
+    if ((st = check_device_buffer(out, "out"))) return st;
     void *ws = nullptr;
-    cslsm_status st = scratch_address(&ws);
+    st = scratch_address(&ws);
     if (st) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     // the array keeps the previous call's contents: zero what must start at 0
