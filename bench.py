@@ -545,8 +545,11 @@ def run_secondary(args) -> None:
                    batched_fp32_value=vox * 60 / (res["fp32"][0] / 1e3),
                    max_dpsnr_bf16_vs_plain=max(abs(a - b) for a, b in zip(res["bf16"][1], ps_plain)),
                    max_dpsnr_fp32_vs_plain=max(abs(a - b) for a, b in zip(res["fp32"][1], ps_plain)))
-    elif name == "unrolled_b8":
-        B, Z, H, W = 8, 16, 512, 512
+    elif name in ("unrolled_b8", "unrolled_b1"):
+        # batch 8 with the dual iterates kept (29 GB of workspace); batch 1 with
+        # them recomputed (a few hundred MB: the case for full profiler captures)
+        B, Z, H, W = (8 if name == "unrolled_b8" else 1), 16, 512, 512
+        keep_default = name == "unrolled_b8"
         g = torch.Generator(device="cuda").manual_seed(11)
         logits = torch.randn(B, Z, H, W, generator=g, device=dev)
         x = torch.rand(B, Z, H, W, generator=g, device=dev)
@@ -570,15 +573,16 @@ def run_secondary(args) -> None:
                     bw.append(e1.elapsed_time(e2))
             return float(np.mean(fw)), float(np.mean(bw))
 
-        # dual iterates kept by the segment recompute (29 GB of workspace), then
-        # recomputed per slice in the reverse sweep
-        fwk, bwk = run(True, max(1, args.steps))
-        fwr, bwr = run(False, 1)
+        # dual iterates kept by the segment recompute (batch 8), then recomputed
+        # per slice in the reverse sweep
+        fwk, bwk = run(keep_default, max(1, args.steps))
         vox = B * Z * H * W
         out.update(metric="unrolled PnP-ADMM voxel-iterations/s (forward + backward)", unit=UNIT,
                    value=vox * 30 / ((fwk + bwk) / 1e3), forward_ms=fwk, backward_ms=bwk,
-                   backward_ms_recompute_duals=bwr, forward_ms_recompute_run=fwr,
-                   keep_duals=True, batch=B, volume=[Z, H, W], iterations=30)
+                   keep_duals=keep_default, batch=B, volume=[Z, H, W], iterations=30)
+        if keep_default:
+            fwr, bwr = run(False, 1)
+            out.update(backward_ms_recompute_duals=bwr, forward_ms_recompute_run=fwr)
     elif name == "wnnm_512x512x16":
         # the WNNM prior (listed in Sec. III-B) on the benchmark volume, z term on
         wk = synth.WORKLOADS["tvz_512x512x16"]
@@ -665,7 +669,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=None,
                     help="secondary workload: tikhonov_1024x1024x32, tv_1024x1024x32, "
-                         "bm3d_1024x1024x32, tv_128x128x8, batched_64, unrolled_b8, "
+                         "bm3d_1024x1024x32, tv_128x128x8, batched_64, unrolled_b8, unrolled_b1, "
                          "cr_sweep_256x256x40, tol_caps_512x512x16, wnnm_512x512x16")
     args = ap.parse_args()
     if args.workload:
