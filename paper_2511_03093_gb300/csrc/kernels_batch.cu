@@ -3,7 +3,7 @@
 // persistent kernel launch, captured once in a CUDA graph and replayed.
 //
 // Work decomposition.  For every item (measurement) an iteration is a chain of
-// phases: the x-update (Eq. v-update, units of 512 pixel columns), then the
+// phases: the x-update (Eq. v-update, units of 256 pixel columns), then the
 // TV u-step cut into phases of at most k Chambolle steps.  A TV unit is one
 // tile of one slice for one phase: it forms g on its region (the tile plus a
 // halo of k + 1 pixels; with gamma > 0 from the newest u_{n-1} and the previous
@@ -20,13 +20,18 @@
 // number.  Many items in flight hide the exchange latency that bounds the
 // single-volume sweep.
 //
-// Scheduling.  The grid is exactly as many CTAs as fit on the GPU at once.
-// Each CTA takes the next unit number from a global ticket counter, waits
-// until the item's completed-unit counter (read with acquire semantics)
-// reaches the count the unit depends on, runs the unit and increments the
-// counter with release semantics after a CTA barrier.  Because units are taken in
-// global order and every CTA is resident, the units waited for are already
-// held by running CTAs: the schedule cannot deadlock.  Every wait is bounded
+// Scheduling.  The grid is exactly as many CTAs as fit on the GPU at once
+// (two 256-thread CTAs per SM, so that one CTA's loads and barriers overlap
+// the other's Chambolle steps).  Each CTA holds a current unit number and
+// reserves the next one from a global ticket counter while it works (the
+// atomic's latency hides behind the unit); a unit number is decoded by one
+// lookup in a per-iteration table of (item, level, index).  Before it starts
+// a unit the CTA waits until the item's completed-unit counter (read with
+// acquire semantics) reaches the count the unit depends on; it increments the
+// counter with release semantics after a CTA barrier.  Units are numbered so
+// that every unit waited for has a smaller number, and a CTA finishes its
+// current unit before it waits for its reserved one, so the smallest unfinished
+// number can always proceed: the schedule cannot deadlock.  Every wait is bounded
 // (a wall-clock limit read from %globaltimer); on expiry the CTA raises the
 // batch's error word, every CTA stops taking units, and the host reports
 // CSLSM_ERR_TIMEOUT.  Data produced inside the launch is read with L2-only
@@ -47,8 +52,8 @@
 namespace cslsm {
 namespace {
 
-constexpr int kBW = 16, kBR = 8;     // warps per CTA, rows of the region per warp
-constexpr int kBNT = kBW * 32;       // 512 threads per CTA
+constexpr int kBW = 8, kBR = 8;      // warps per CTA, rows of the region per warp
+constexpr int kBNT = kBW * 32;       // 256 threads per CTA, two CTAs per SM
 constexpr int kBRH = kBW * kBR + 2;  // region rows
 constexpr int kBPW = 64;             // region columns
 
@@ -66,13 +71,17 @@ struct BItem {
     long long units_iter;
 };
 
+// Unit of an iteration: item (16 bits), level (16 bits), index within the
+// item's level (32 bits).
+__host__ __device__ inline unsigned long long pack_unit(int item, int level, int idx)
+{
+    return ((unsigned long long)item << 48) | ((unsigned long long)level << 32) | (unsigned)idx;
+}
+
 struct BDesc {
     const BItem *items;
     int n, iters, levels;
-    const long long *level_cum;  // [levels + 1] units before each level within an iteration
-    const int *lvl_start;        // [levels + 1] first entry of each level
-    const int *ent_item;         // entries: item of the entry
-    const long long *ent_cum;    // entries: first unit of the entry within its level
+    const unsigned long long *unit_tab;  // [units_iter] units of one iteration, in order
     long long units_iter, total;
     unsigned long long *ticket;
     unsigned long long *done;  // [n]
@@ -121,6 +130,7 @@ __device__ void xupdate_unit(const BItem &it, int unit, float rho, bool last)
         const uint32_t word = __ldcg(it.words + (size_t)j * it.wstride + pix);
         const size_t base = (size_t)j * it.R * HW + pix;
         float s = 0.f;
+#pragma unroll 8
         for (int r = 0; r < it.R; ++r) {
             if ((word >> r) & 1u) {
                 const size_t o = base + (size_t)r * HW;
@@ -128,6 +138,7 @@ __device__ void xupdate_unit(const BItem &it, int unit, float rho, bool last)
             }
         }
         const float e = (__ldcg(it.b + (size_t)j * HW + pix) - s) / (rho + (float)__popc(word));
+#pragma unroll 8
         for (int r = 0; r < it.R; ++r) {
             const size_t o = base + (size_t)r * HW;
             const float dr = ld_l2<S>(d + o);
@@ -308,40 +319,29 @@ __device__ void tv_unit(const BItem &it, const BDesc &D, int n, int j, int tile,
 }
 
 template <typename S>
-__global__ void __launch_bounds__(kBNT) batch_persistent_kernel(const BDesc *__restrict__ dp)
+__global__ void __launch_bounds__(kBNT, 2) batch_persistent_kernel(const BDesc *__restrict__ dp)
 {
     __shared__ Bnd<kBW> sb;
     __shared__ long long s_t;
     __shared__ int s_abort;
     const BDesc D = *dp;
     const bool zsweep = D.gam > 0.f;
+    unsigned long long next = 0;  // thread 0: the reserved unit number
+    if (threadIdx.x == 0) next = atomicAdd(D.ticket, 1ull);
     for (;;) {
         if (threadIdx.x == 0) {
             s_abort = *(volatile int *)D.error;
-            s_t = s_abort ? D.total : (long long)atomicAdd(D.ticket, 1ull);
+            s_t = s_abort ? D.total : (long long)next;
         }
         __syncthreads();
         const long long t = s_t;
         if (t >= D.total) break;
-        // decode the unit number
+        // reserve the following unit now; the value is read after this unit
+        if (threadIdx.x == 0) next = atomicAdd(D.ticket, 1ull);
         const int k = (int)(t / D.units_iter);
-        long long r = t - (long long)k * D.units_iter;
-        int lo = 0, hi = D.levels - 1;
-        while (lo < hi) {  // last level with level_cum <= r
-            const int mid = (lo + hi + 1) / 2;
-            if (D.level_cum[mid] <= r) lo = mid;
-            else hi = mid - 1;
-        }
-        const int p = lo;
-        r -= D.level_cum[p];
-        int e0 = D.lvl_start[p], e1 = D.lvl_start[p + 1] - 1;
-        while (e0 < e1) {
-            const int mid = (e0 + e1 + 1) / 2;
-            if (D.ent_cum[mid] <= r) e0 = mid;
-            else e1 = mid - 1;
-        }
-        const int i = D.ent_item[e0];
-        const int unit = (int)(r - D.ent_cum[e0]);
+        const unsigned long long ent = __ldg(D.unit_tab + (t - (long long)k * D.units_iter));
+        const int i = (int)(ent >> 48), p = (int)((ent >> 32) & 0xffffu);
+        const int unit = (int)(ent & 0xffffffffu);
         const BItem &it = D.items[i];
         // wait for the item's previous levels (and iteration)
         if (threadIdx.x == 0) {
@@ -454,49 +454,30 @@ cslsm_status batch_build(const BatchSpec &spec, BatchRun &run)
         if (P > 1) pbytes += (4 * (size_t)(chain ? 1 : b.Z) * s.H * s.W * sizeof(float) + 255) &
                              ~size_t(255);
     }
-    // level tables: per level p, the items having level p and their unit counts
-    std::vector<long long> level_cum(levels + 1, 0);
-    std::vector<int> lvl_start(levels + 1, 0), ent_item;
-    std::vector<long long> ent_cum;
-    for (int p = 0; p < levels; ++p) {
-        lvl_start[p] = (int)ent_item.size();
-        long long acc = 0;
+    // the units of one iteration in order: level-major, then item, then index
+    std::vector<unsigned long long> tab;
+    for (int p = 0; p < levels; ++p)
         for (int i = 0; i < n; ++i) {
             const BItem &b = items[i];
             const long long lv = (b.units_iter - b.units_x) / b.units_lvl;
             const long long c = p == 0 ? b.units_x : (p - 1 < lv ? b.units_lvl : 0);
-            if (c == 0) continue;
-            ent_item.push_back(i);
-            ent_cum.push_back(acc);
-            acc += c;
+            for (long long u = 0; u < c; ++u) tab.push_back(pack_unit(i, p, (int)u));
         }
-        level_cum[p + 1] = level_cum[p] + acc;
-    }
-    lvl_start[levels] = (int)ent_item.size();
-    const long long units_iter = level_cum[levels];
+    const long long units_iter = (long long)tab.size();
     // one device allocation for descriptors, tables, counters and the items'
     // dual-field exchange buffers
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
-    const size_t sz_items = al(sizeof(BItem) * n), sz_lc = al(sizeof(long long) * (levels + 1)),
-                 sz_ls = al(sizeof(int) * (levels + 1)), sz_ei = al(sizeof(int) * ent_item.size()),
-                 sz_ec = al(sizeof(long long) * ent_cum.size()), sz_cnt = al(8 * (n + 1)),
-                 sz_err = 256, sz_desc = al(sizeof(BDesc));
-    const size_t total =
-        sz_items + sz_lc + sz_ls + sz_ei + sz_ec + sz_cnt + sz_err + sz_desc + pbytes;
+    const size_t sz_items = al(sizeof(BItem) * n), sz_tab = al(sizeof(unsigned long long) * tab.size()),
+                 sz_cnt = al(8 * (n + 1)), sz_err = 256, sz_desc = al(sizeof(BDesc));
+    const size_t total = sz_items + sz_tab + sz_cnt + sz_err + sz_desc + pbytes;
     char *base = nullptr;
     CSLSM_CUDA(cudaMalloc(&base, total));
     run.mem = base;
     char *q = base;
     BItem *d_items = (BItem *)q;
     q += sz_items;
-    long long *d_lc = (long long *)q;
-    q += sz_lc;
-    int *d_ls = (int *)q;
-    q += sz_ls;
-    int *d_ei = (int *)q;
-    q += sz_ei;
-    long long *d_ec = (long long *)q;
-    q += sz_ec;
+    unsigned long long *d_tab = (unsigned long long *)q;
+    q += sz_tab;
     unsigned long long *d_cnt = (unsigned long long *)q;  // [0] ticket, [1..n] done
     q += sz_cnt;
     int *d_err = (int *)q;
@@ -509,10 +490,7 @@ cslsm_status batch_build(const BatchSpec &spec, BatchRun &run)
     D.n = n;
     D.iters = spec.iters;
     D.levels = levels;
-    D.level_cum = d_lc;
-    D.lvl_start = d_ls;
-    D.ent_item = d_ei;
-    D.ent_cum = d_ec;
+    D.unit_tab = d_tab;
     D.units_iter = units_iter;
     D.total = units_iter * spec.iters;
     D.ticket = d_cnt;
@@ -528,13 +506,7 @@ cslsm_status batch_build(const BatchSpec &spec, BatchRun &run)
     D.k = k;
     D.P = P;
     CSLSM_CUDA(cudaMemcpy(d_items, items.data(), sizeof(BItem) * n, cudaMemcpyHostToDevice));
-    CSLSM_CUDA(cudaMemcpy(d_lc, level_cum.data(), sizeof(long long) * (levels + 1),
-                          cudaMemcpyHostToDevice));
-    CSLSM_CUDA(cudaMemcpy(d_ls, lvl_start.data(), sizeof(int) * (levels + 1),
-                          cudaMemcpyHostToDevice));
-    CSLSM_CUDA(cudaMemcpy(d_ei, ent_item.data(), sizeof(int) * ent_item.size(),
-                          cudaMemcpyHostToDevice));
-    CSLSM_CUDA(cudaMemcpy(d_ec, ent_cum.data(), sizeof(long long) * ent_cum.size(),
+    CSLSM_CUDA(cudaMemcpy(d_tab, tab.data(), sizeof(unsigned long long) * tab.size(),
                           cudaMemcpyHostToDevice));
     CSLSM_CUDA(cudaMemcpy(d_desc, &D, sizeof(BDesc), cudaMemcpyHostToDevice));
     run.desc = d_desc;

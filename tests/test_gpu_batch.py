@@ -6,8 +6,9 @@ wait that runs out as CSLSM_ERR_TIMEOUT without hanging."""
 import numpy as np
 import pytest
 
+import oracle
 import synth
-from tests.gpu_util import to_dev, to_np
+from tests.gpu_util import DPSNR, REL_ITER, rel_l2, to_dev, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -135,3 +136,55 @@ def test_batch_rejects_unsupported(cs):
     for prm in (cs.Params(denoiser="bm3d"), cs.Params(denoiser="tv", tol=1e-3)):
         with pytest.raises(cs.CslsmError):
             cs.Batch(items, prm)
+
+
+ORACLE_SIZES = [(8, 64, 64), (4, 130, 101), (16, 48, 72)]
+
+
+def _oracle_items(cs, seed0):
+    import torch
+
+    items, datas = [], []
+    for k, (Z, H, W) in enumerate(ORACLE_SIZES):
+        w = synth.Workload(f"o{k}", Z, H, W, drift=True, mask_p=0.3, peak=50.0, sigma_g=0.02,
+                           seed=seed0 + k, n_blobs=max(4, Z * H * W // 400))
+        data = synth.generate(w)
+        plan = cs.Plan(H, W, 1, Z, to_dev(data["masks"]))
+        items.append((plan, to_dev(data["b"]), torch.empty((Z, H, W), dtype=torch.float32,
+                                                           device="cuda")))
+        datas.append(data)
+    return items, datas
+
+
+def test_batch_items_match_fp64_oracle_one_iteration(cs):
+    """Every item of an uneven FP32 batch, one iteration of Algorithm 1 (TV + z),
+    against the FP64 oracle run on the same measurement."""
+    items, datas = _oracle_items(cs, 900)
+    prm = cs.Params(rho=1.0, lam=0.05, gamma=0.2, iters=1, denoiser="tv", tv_inner=20)
+    batch = cs.Batch(items, prm)
+    batch.run()
+    batch.wait()
+    for (plan, b, v), data, (Z, H, W) in zip(items, datas, ORACLE_SIZES):
+        ref, *_ = oracle.admm(data["b64"], data["masks"], Z, rho=1.0, lam=0.05, gamma=0.2,
+                              iters=1, denoiser="tv", tv_inner=20)
+        assert rel_l2(to_np(v), ref) <= REL_ITER, (Z, H, W)
+    batch.close()
+
+
+@pytest.mark.parametrize("storage", ["fp32", "bf16"])
+def test_batch_items_full_run_psnr_matches_fp64_oracle(cs, storage):
+    """Whole 40-iteration solves of every item: reconstruction PSNR within 0.05 dB
+    of the FP64 oracle's, for FP32 and for BF16 state storage."""
+    items, datas = _oracle_items(cs, 950)
+    prm = cs.Params(rho=1.0, lam=0.05, gamma=0.2, iters=40, denoiser="tv", tv_inner=20,
+                    storage=storage)
+    batch = cs.Batch(items, prm)
+    batch.run()
+    batch.wait()
+    for (plan, b, v), data, (Z, H, W) in zip(items, datas, ORACLE_SIZES):
+        ref, *_ = oracle.admm(data["b64"], data["masks"], Z, rho=1.0, lam=0.05, gamma=0.2,
+                              iters=40, denoiser="tv", tv_inner=20)
+        p_gpu = oracle.psnr(to_np(v), data["x"])
+        p_ref = oracle.psnr(ref, data["x"])
+        assert abs(p_gpu - p_ref) <= DPSNR, (storage, Z, H, W, p_gpu, p_ref)
+    batch.close()

@@ -52,6 +52,21 @@ def test_match_lists_bit_exact(cs, Z, H, W, stage):
         np.testing.assert_array_equal(lists[z], idx)
 
 
+@pytest.mark.parametrize("stage", [1, 2])
+def test_match_lists_bit_exact_outside_unit_range(cs, stage):
+    """ADMM iterates leave [0, 1]: the 8-bit matching codes saturate at 0 and 255
+    there; lists must still equal the oracle's bit for bit."""
+    img = _blobs(77, 2, 64, 70, noise=0.02 if stage == 1 else 0.005)
+    img = (1.8 * img - 0.4).astype(np.float32)  # about [-0.4, 1.4]
+    assert img.min() < 0.0 and img.max() > 1.0
+    lists, counts = cs.bm3d_match(to_dev(img), stage)
+    lists, counts = lists.cpu().numpy(), counts.cpu().numpy()
+    for z in range(2):
+        idx, cnt = oracle.bm3d_match(img[z], stage)
+        np.testing.assert_array_equal(counts[z], cnt)
+        np.testing.assert_array_equal(lists[z], idx)
+
+
 def test_match_ties_on_constant_image(cs):
     img = np.full((1, 40, 44), 0.25, dtype=np.float32)
     lists, counts = cs.bm3d_match(to_dev(img), 1)

@@ -95,6 +95,29 @@ def test_kept_duals_give_the_same_gradients(cs, B, Z, H, W, every):
     assert out[0][2:] == out[1][2:]
 
 
+def test_full_length_gradient_matches_fp64_oracle(cs):
+    """The full-length unrolled map (30 iterations, 20 Huber-TV steps, checkpoints
+    every 5) at the reduced oracle size 64 x 64 x 8, batch 1: v and every gradient
+    against the FP64 oracle's autograd gradient."""
+    B, Z, H, W = 1, 8, 64, 64
+    logits, b, x = _problem(21, B, Z, H, W)
+    cfg = dict(iters=30, tv_steps=20, tv_tau=0.125, huber_eps=1e-3, ckpt_every=5)
+    lg = logits.cuda().requires_grad_(True)
+    r, l_, gm = _scalars(1.0, 0.05, 0.2)
+    v = cs.unrolled_admm(lg, b.cuda(), r, l_, gm, **cfg)
+    (0.5 * ((v - x.cuda()) ** 2).sum()).backward()
+    lg64 = logits.double().requires_grad_(True)
+    r64, l64, g64 = _scalars(1.0, 0.05, 0.2, dev="cpu", dtype=torch.float64)
+    v64 = un.unrolled_admm(lg64, b.double(), r64, l64, g64, iters=cfg["iters"],
+                           T=cfg["tv_steps"], tau=cfg["tv_tau"], eps=cfg["huber_eps"])
+    (0.5 * ((v64 - x.double()) ** 2).sum()).backward()
+    assert rel_l2(v.detach().cpu().numpy(), v64.detach().numpy()) <= 1e-5
+    assert rel_l2(lg.grad.cpu().numpy(), lg64.grad.numpy()) <= 1e-3
+    for a, e in ((r, r64), (l_, l64), (gm, g64)):
+        ga, ge = float(a.grad), float(e.grad)
+        assert abs(ga - ge) <= 1e-3 * max(abs(ge), 1e-3), (ga, ge)
+
+
 def test_finite_differences_on_gpu(cs):
     """Central differences with 1e-4 relative perturbations of rho, lambda, gamma."""
     logits, b, x = _problem(8, 1, 4, 32, 28)
@@ -143,6 +166,18 @@ def test_full_size_batch8(cs):
         lm = 0.5 * ((cs.unrolled_admm(logits, b, *_scalars(1.0, 0.05 - h, 0.2), **cfg) - x) ** 2).mean()
     fd = (float(lp) - float(lm)) / (2 * h)
     assert abs(fd - float(l_.grad)) <= 5e-2 * max(abs(float(l_.grad)), 1e-6), (fd, float(l_.grad))
+    # and along rho and gamma
+    for k, (base, an) in enumerate(((1.0, float(r.grad)), (0.2, float(gm.grad)))):
+        h = 1e-3 * base
+        vals = [[1.0, 0.05, 0.2], [1.0, 0.05, 0.2]]
+        idx = 0 if k == 0 else 2
+        vals[0][idx] += h
+        vals[1][idx] -= h
+        with torch.no_grad():
+            lp, lm = (0.5 * ((cs.unrolled_admm(logits, b, *_scalars(*vv), **cfg) - x) ** 2).mean()
+                      for vv in vals)
+        fd = (float(lp) - float(lm)) / (2 * h)
+        assert abs(fd - an) <= 5e-2 * max(abs(an), 1e-6), (("rho", "gamma")[k], fd, an)
     # the same gradients with the dual iterates kept (about 29 GB of workspace)
     lg2 = logits.clone().requires_grad_(True)
     r2, l2, g2 = _scalars(1.0, 0.05, 0.2)
