@@ -1,18 +1,24 @@
 #!/usr/bin/env python
 """PnP-ADMM reconstruction throughput on GB300 (voxel-iterations per second).
 
-Workload (one "step"): the 512 x 512 x 16 drifting-blob volume behind one
-coded measurement (Bernoulli(0.3) DMD patterns, Poisson peak 50 + Gaussian
-sigma 0.02), reconstructed by 100 iterations of Algorithm 1 with the TV prior
-and the z-smoothness Gauss-Seidel sweep (rho = 1, lambda = 0.05, gamma = 0.2,
-20 Chambolle steps per prox).  A step re-packs the DMD patterns and runs the
-whole solve through the C ABI.  Inputs are seeded synthetic data.
+Workload (one "step"): 64 independent coded measurements of uneven size
+(H = W in {256, 512, 768, 1024}, Z in {8, 16, 32} slices, drawn with seed
+4000; 614 M voxels in all) reconstructed by 60 iterations of Algorithm 1 with
+the TV prior and the z-smoothness Gauss-Seidel sweep (rho = 1, lambda = 0.05,
+gamma = 0.2, 20 Chambolle steps per prox), all of them in ONE persistent
+launch replayed from a CUDA graph (the batched solver), iterates u, d, w
+stored in BF16 with FP32 arithmetic.  A step re-packs every item's DMD
+patterns and runs the batch through the C ABI.  Inputs are seeded synthetic
+data (drifting Gaussian blobs, Bernoulli(0.3) patterns, Poisson peak 50 +
+Gaussian 0.02).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload NAME]
 
-N > 1 runs under torchrun, one independent measurement per rank (weak
-scaling, no data-path collective).  --impl reference times the FP64 CPU
-oracle on the same workload (bounded sample per step) on the host cores.
+N > 1 runs under torchrun, one independent batch per rank (weak scaling, no
+data-path collective).  --impl reference times the FP64 CPU oracle on a
+stratified 8-item sample of the batch (bounded iterations) on the host cores.
+--workload runs one of the other configurations instead (one JSON line).
 """
 from __future__ import annotations
 
@@ -29,15 +35,21 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "tvz_512x512x16"
-PARAMS = dict(rho=1.0, lam=0.05, gamma=0.2, iters=100, denoiser="tv", tv_inner=20,
-              tv_tau=0.125)
+WORKLOAD = "batched_64"
+PARAMS = dict(rho=1.0, lam=0.05, gamma=0.2, iters=60, denoiser="tv", tv_inner=20,
+              tv_tau=0.125, storage="bf16")
+# the single-volume 512 x 512 x 16 configuration (a secondary workload)
+PARAMS_TVZ = dict(rho=1.0, lam=0.05, gamma=0.2, iters=100, denoiser="tv", tv_inner=20,
+                  tv_tau=0.125)
 METRIC = "PnP-ADMM voxel-iterations/s"
 UNIT = "voxel-it/s"
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
-DOMINANT = "tvz_sweep"  # one launch = the TV u-step of all 16 slices (z Gauss-Seidel sweep)
-DOMINANT_SOURCES = ("kernels_tvz.cu", "tv_body.cuh")
-TIMING_PERIOD = 4  # sample every 4th launch of each kernel with CUDA events
+DOMINANT = "batch_persistent"  # one launch = the whole 60-iteration batch
+DOMINANT_SOURCES = ("kernels_batch.cu", "tv_body.cuh")
+TVZ_DOMINANT = "tvz_sweep"  # the single-volume configuration's dominant kernel
+TVZ_SOURCES = ("kernels_tvz.cu", "tv_body.cuh")
+TIMING_PERIOD = 1  # every launch of each kernel timed with CUDA events
+ORACLE_SAMPLE_ITERS = 2  # bounded CPU sample: ADMM iterations per sampled item
 
 
 def _env_int(k, d):
@@ -47,13 +59,25 @@ def _env_int(k, d):
         return d
 
 
-def _config(world: int) -> dict:
-    return {"workload": f"{WORKLOAD}: TV + z-smoothness PnP-ADMM, 512x512x16, "
-                        f"{PARAMS['iters']} iterations, {PARAMS['tv_inner']} TV steps",
-            "volume": [16, 512, 512], "iterations": PARAMS["iters"],
+def _config(world: int, voxels: int) -> dict:
+    return {"workload": f"{WORKLOAD}: 64 independent measurements, H = W in "
+                        "{256,512,768,1024} x Z in {8,16,32} (seed 4000), TV + z-smoothness "
+                        f"PnP-ADMM, {PARAMS['iters']} iterations, {PARAMS['tv_inner']} TV steps, "
+                        "one persistent launch under a CUDA graph",
+            "items": 64, "voxels": voxels, "iterations": PARAMS["iters"],
             "tv_inner": PARAMS["tv_inner"], "rho": PARAMS["rho"], "lambda": PARAMS["lam"],
-            "gamma": PARAMS["gamma"], "l2": "flushed between steps (512 MiB write)",
+            "gamma": PARAMS["gamma"], "storage": "bf16 iterates (u, d, w), fp32 arithmetic",
+            "l2": "inputs larger than L2 (2.5 GB per field) and L2 flushed between steps",
             "parallelism": f"replicas x{world}"}
+
+
+def _config_tvz(world: int) -> dict:
+    return {"workload": "tvz_512x512x16: TV + z-smoothness PnP-ADMM, 512x512x16, "
+                        f"{PARAMS_TVZ['iters']} iterations, {PARAMS_TVZ['tv_inner']} TV steps",
+            "volume": [16, 512, 512], "iterations": PARAMS_TVZ["iters"],
+            "tv_inner": PARAMS_TVZ["tv_inner"], "rho": PARAMS_TVZ["rho"],
+            "lambda": PARAMS_TVZ["lam"], "gamma": PARAMS_TVZ["gamma"],
+            "l2": "flushed between steps (512 MiB write)", "parallelism": f"replicas x{world}"}
 
 
 def tv_flops_per_launch(H: int, W: int, T: int) -> float:
@@ -89,15 +113,15 @@ def _kernel_hash(sources=DOMINANT_SOURCES) -> str:
     return h.hexdigest()[:16]
 
 
-def _traffic():
-    """DRAM bytes per launch of the dominant kernel from the committed ncu summary,
-    if it was taken on the kernel source as it is now."""
-    p = os.path.join(ROOT, "profiles", f"{DOMINANT}_{WORKLOAD}.json")
+def _traffic(kernel: str, workload: str, sources) -> float | None:
+    """DRAM bytes per launch of a kernel from its committed ncu record, if that
+    record was taken on the kernel's sources as they are now."""
+    p = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.json")
     try:
         rec = json.load(open(p))
     except (OSError, ValueError):
         return None
-    if rec.get("sources_sha256_16") != _kernel_hash():
+    if rec.get("sources_sha256_16") != _kernel_hash(sources):
         return None
     return rec.get("dram_bytes_per_launch")
 
@@ -183,13 +207,46 @@ def summarize_clocks(lines, t0=None, t1=None):
 
 
 def rank_workload(rank: int):
-    """Each rank reconstructs its own independent measurement (replicas)."""
+    """The single-volume configuration: each rank its own measurement."""
     import dataclasses
 
     import synth
 
-    w = synth.WORKLOADS[WORKLOAD]
+    w = synth.WORKLOADS["tvz_512x512x16"]
     return dataclasses.replace(w, seed=w.seed + 100 * rank) if rank else w
+
+
+def rank_workloads(rank: int):
+    """Each rank reconstructs its own independent batch (replicas): seed 4000
+    for rank 0, 4000 + 1000 r for rank r."""
+    import synth
+
+    return synth.batch_workloads(seed=4000 + 1000 * rank)
+
+
+def _gen_compact(w):
+    """One batch item's inputs, as the bench keeps them (float32 ground truth)."""
+    import synth
+
+    d = synth.generate(w)
+    return {"x": d["x"].astype("float32"), "masks": d["masks"], "b": d["b"]}
+
+
+def _gen_items(ws):
+    """Generates the items in a process pool started with spawn (independent of
+    any CUDA state of this process)."""
+    import multiprocessing as mp
+
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 4)) as pool:
+        return pool.map(_gen_compact, ws)
+
+
+def oracle_sample(ws) -> list[int]:
+    """8 items stratified by size: the items are ordered by voxel count (then
+    index) and the middle item of each eighth is taken."""
+    order = sorted(range(len(ws)), key=lambda i: (ws[i].Z * ws[i].H * ws[i].W, i))
+    n = len(order)
+    return [order[(2 * k + 1) * n // 16] for k in range(8)]
 
 
 def max_over_ranks(values, world: int, device=None):
@@ -208,13 +265,13 @@ def job_throughput(units_per_rank: float, world: int, max_ms: float) -> float:
     return units_per_rank * world / (max_ms / 1e3)
 
 
-def cpu_baseline(data, iters: int) -> dict:
+def cpu_baseline_tvz(data, iters: int) -> dict:
     import oracle
 
     t0 = time.perf_counter()
-    oracle.admm(data["b64"], data["masks"], 16, rho=PARAMS["rho"], lam=PARAMS["lam"],
-                gamma=PARAMS["gamma"], iters=iters, denoiser="tv", tv_inner=PARAMS["tv_inner"],
-                tv_tau=PARAMS["tv_tau"])
+    oracle.admm(data["b64"], data["masks"], 16, rho=PARAMS_TVZ["rho"], lam=PARAMS_TVZ["lam"],
+                gamma=PARAMS_TVZ["gamma"], iters=iters, denoiser="tv",
+                tv_inner=PARAMS_TVZ["tv_inner"], tv_tau=PARAMS_TVZ["tv_tau"])
     dt = time.perf_counter() - t0
     vox = data["masks"].size
     return {"value": vox * iters / dt, "unit": UNIT, "cores": _omp_threads(), "kind": "oracle",
@@ -222,41 +279,68 @@ def cpu_baseline(data, iters: int) -> dict:
                       f"({dt:.1f} s)"}
 
 
+def oracle_batch_sample(ws, datas, idx, iters: int) -> tuple[float, int]:
+    """Runs the FP64 oracle (Algorithm 1, TV + z) for `iters` iterations on each
+    sampled item; returns (seconds, voxel-iterations)."""
+    import numpy as np
+
+    import oracle
+
+    t0 = time.perf_counter()
+    units = 0
+    for i, d in zip(idx, datas):
+        w = ws[i]
+        oracle.admm(d["b"].astype(np.float64), d["masks"], w.Z, rho=PARAMS["rho"],
+                    lam=PARAMS["lam"], gamma=PARAMS["gamma"], iters=iters, denoiser="tv",
+                    tv_inner=PARAMS["tv_inner"], tv_tau=PARAMS["tv_tau"])
+        units += w.Z * w.H * w.W * iters
+    return time.perf_counter() - t0, units
+
+
+def cpu_baseline(ws, datas) -> dict:
+    """The oracle on the stratified 8-item sample (datas: all items)."""
+    idx = oracle_sample(ws)
+    dt, units = oracle_batch_sample(ws, [datas[i] for i in idx], idx, ORACLE_SAMPLE_ITERS)
+    return {"value": units / dt, "unit": UNIT, "cores": _omp_threads(), "kind": "oracle",
+            "sample": f"FP64 oracle, {ORACLE_SAMPLE_ITERS} of {PARAMS['iters']} ADMM iterations "
+                      f"(FP64 state) of 8 items stratified by size (items {idx}, "
+                      f"{units / ORACLE_SAMPLE_ITERS / 1e6:.1f} M voxels; {dt:.1f} s)"}
+
+
 def _omp_threads() -> int:
     return int(os.environ.get("OMP_NUM_THREADS", len(os.sched_getaffinity(0))))
 
 
 def run_reference(args) -> None:
-    """The FP64 CPU oracle as the reference arm (rank 0 only)."""
+    """The FP64 CPU oracle as the reference arm (rank 0 only): each step runs the
+    oracle on the batch's stratified 8-item sample for a bounded number of
+    iterations."""
     if _env_int("RANK", 0) != 0:
         return
-    import synth
-
-    data = synth.generate(WORKLOAD)
+    ws = rank_workloads(0)
+    idx = oracle_sample(ws)
+    datas = _gen_items([ws[i] for i in idx])
     import oracle
 
     oracle.lib()
-    iters = 20  # bounded sample per step: 20 of the 100 ADMM iterations
-    vox = data["masks"].size
 
     def step():
-        t0 = time.perf_counter()
-        oracle.admm(data["b64"], data["masks"], 16, rho=PARAMS["rho"], lam=PARAMS["lam"],
-                    gamma=PARAMS["gamma"], iters=iters, denoiser="tv",
-                    tv_inner=PARAMS["tv_inner"], tv_tau=PARAMS["tv_tau"])
-        return time.perf_counter() - t0
+        return oracle_batch_sample(ws, datas, idx, ORACLE_SAMPLE_ITERS)
 
     for _ in range(args.warmup):
         step()
-    ts = [step() for _ in range(args.steps)]
-    total = sum(ts)
-    value = vox * iters * args.steps / total
-    sample = f"FP64 oracle, {iters} of {PARAMS['iters']} ADMM iterations per step"
+    runs = [step() for _ in range(args.steps)]
+    total = sum(t for t, _ in runs)
+    units = sum(u for _, u in runs)
+    value = units / total
+    sample = (f"FP64 oracle, {ORACLE_SAMPLE_ITERS} of {PARAMS['iters']} ADMM iterations of 8 "
+              f"items stratified by size (items {idx}) per step")
+    vox = sum(w.Z * w.H * w.W for w in ws)
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": _config(1),
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": _config(1, vox),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": _omp_threads(),
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -265,6 +349,198 @@ def run_reference(args) -> None:
 
 
 def run_ours(args) -> None:
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank, world = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1)
+    local = _env_int("LOCAL_RANK", 0)
+    ws = rank_workloads(rank)
+    datas = _gen_items(ws)  # host-side generation before any CUDA call
+
+    import paper_2511_03093_gb300 as cs
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    cs.lib()
+
+    n = len(ws)
+    vox = sum(w.Z * w.H * w.W for w in ws)
+    masks_h = [torch.from_numpy(d["masks"]).pin_memory() for d in datas]
+    b_h = [torch.from_numpy(d["b"]).pin_memory() for d in datas]
+    v_h = [torch.empty((w.Z, w.H, w.W), dtype=torch.float32).pin_memory() for w in ws]
+    masks_d = [m.to(dev) for m in masks_h]
+    b_d = [b.to(dev) for b in b_h]
+    v_d = [torch.empty((w.Z, w.H, w.W), dtype=torch.float32, device=dev) for w in ws]
+    plans = [cs.Plan(w.H, w.W, 1, w.Z, m) for w, m in zip(ws, masks_d)]
+    items = list(zip(plans, b_d, v_d))
+    cs.set_autotune(1)  # steps per phase timed on the batch itself at creation
+    prm = cs.Params(**PARAMS)
+    batch = cs.Batch(items, prm)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        for plan, m in zip(plans, masks_d):
+            plan.set_masks(m)
+        batch.run()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    gpu_id = None
+    try:
+        gpu_id = str(torch.cuda.get_device_properties(dev).uuid)
+        if gpu_id and not gpu_id.startswith("GPU-"):
+            gpu_id = "GPU-" + gpu_id
+    except Exception:
+        gpu_id = None
+    clocks = ClockSampler(gpu_id) if rank == 0 else None
+    for _ in range(max(args.warmup, 0)):
+        step()
+    batch.wait()
+
+    ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    cs.timing_read(DOMINANT, reset=True)
+    barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.time()
+    n0 = cs.launch_count()
+    cs.timing_enable(TIMING_PERIOD)
+    for k in range(args.steps):
+        flush.zero_()
+        ev_s[k].record(stream)
+        step()
+        ev_e[k].record(stream)
+    torch.cuda.synchronize()
+    t_wall1 = time.time()
+    barrier()
+    cs.timing_enable(0)
+    launches = cs.launch_count() - n0
+    batch.wait()  # raises if a device-side wait ran out
+    if clocks:
+        clocks.window(t_wall0, t_wall1)
+    clk = clocks.stop() if clocks else None
+    step_ms = [ev_s[k].elapsed_time(ev_e[k]) for k in range(args.steps)]
+    total_ms = sum(step_ms)
+    n_dom, ms_dom = cs.timing_read(DOMINANT, reset=True)
+
+    # end to end through the public API: every item's patterns and measurement
+    # copied in from pinned host memory, every reconstruction copied back
+    e2e_ms = []
+    for k in range(args.steps):
+        flush.zero_()
+        s_ev, e_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s_ev.record(stream)
+        for i in range(n):
+            masks_d[i].copy_(masks_h[i], non_blocking=True)
+            b_d[i].copy_(b_h[i], non_blocking=True)
+        step()
+        for i in range(n):
+            v_h[i].copy_(v_d[i], non_blocking=True)
+        e_ev.record(stream)
+        e_ev.synchronize()
+        e2e_ms.append(s_ev.elapsed_time(e_ev))
+    batch.wait()
+    e2e_total = sum(e2e_ms)
+
+    total_ms, e2e_total = max_over_ranks([total_ms, e2e_total], world, dev)
+    units = vox * PARAMS["iters"] * args.steps
+    value = job_throughput(units, world, total_ms)
+    e2e_value = job_throughput(units, world, e2e_total)
+
+    if rank == 0:
+        peaks = _peaks()
+        roof = None
+        if n_dom:
+            avg_s = ms_dom / n_dom / 1e3
+            bytes_launch = PARAMS["iters"] * sum(
+                w.Z * w.H * w.W * tv_stream_bytes(w.Z, PARAMS["tv_inner"], True) for w in ws)
+            achieved = bytes_launch / avg_s / 1e9
+            tr = _traffic(DOMINANT, WORKLOAD, DOMINANT_SOURCES)
+            roof = {"bound": "hbm", "kernel": DOMINANT, "achieved": achieved,
+                    "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                    "traffic": tr, "bytes_per_launch": bytes_launch,
+                    "avg_launch_us": avg_s * 1e6, "launches_timed": n_dom,
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy, burst)",
+                    "model": "streaming TV + z prox (one HBM pass per Chambolle step, FP32): "
+                             "44.125 + 4/R + 20 (T - 1) + 8 B per voxel-iteration, per item",
+                    "share_of_step": ms_dom / total_ms}
+            if tr:
+                roof["traffic_per_voxel_it_B"] = tr / (vox * PARAMS["iters"])
+        # the comparison the metric names: plain per-volume FP32 solves of the same
+        # items, and the batch with FP32 state, each run once (not in the timed region)
+        x_d = [torch.from_numpy(d["x"]).to(dev) for d in datas]
+        ps_batch = [float(cs.psnr(v, x)) for v, x in zip(v_d, x_d)]
+        plain = cs.Params(**dict(PARAMS, storage="fp32"))
+        v_p = [torch.empty_like(v) for v in v_d]
+        for plan, b, v in zip(plans, b_d, v_p):  # warm-up of the per-volume path
+            plan.solve(b, plain, v_out=v)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for plan, b, v in zip(plans, b_d, v_p):
+            plan.solve(b, plain, v_out=v)
+        e1.record(stream)
+        e1.synchronize()
+        plain_ms = e0.elapsed_time(e1)
+        ps_plain = [float(cs.psnr(v, x)) for v, x in zip(v_p, x_d)]
+        batch32 = cs.Batch(list(zip(plans, b_d, v_p)), plain)
+        batch32.run()
+        batch32.wait()
+        e0.record(stream)
+        batch32.run()
+        e1.record(stream)
+        e1.synchronize()
+        b32_ms = e0.elapsed_time(e1)
+        batch32.wait()
+        ps_b32 = [float(cs.psnr(v, x)) for v, x in zip(v_p, x_d)]
+        batch32.close()
+        cpu = cpu_baseline(ws, datas) if world == 1 else None
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded Gaussian-blob volumes, Bernoulli DMD masks)",
+            "config": _config(world, vox), "roofline": roof, "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT,
+                    "h2d_bytes_per_step": int(sum(m.numel() + b.numel() * 4
+                                                  for m, b in zip(masks_h, b_h))),
+                    "d2h_bytes_per_step": int(sum(v.numel() * 4 for v in v_h))},
+            "gpu_launches": int(launches), "clocks": clk,
+            "step_ms": [round(x, 3) for x in step_ms],
+            "vs_plain": {"plain_fp32_ms": plain_ms,
+                         "plain_fp32_value": vox * PARAMS["iters"] / (plain_ms / 1e3),
+                         "batched_fp32_ms": b32_ms,
+                         "batched_fp32_value": vox * PARAMS["iters"] / (b32_ms / 1e3),
+                         "speedup_bf16_vs_plain_fp32": plain_ms / (total_ms / args.steps),
+                         "max_dpsnr_bf16_vs_plain_fp32_db": max(abs(a - b) for a, b in
+                                                                zip(ps_batch, ps_plain)),
+                         "max_dpsnr_fp32_batched_vs_plain_db": max(abs(a - b) for a, b in
+                                                                   zip(ps_b32, ps_plain))},
+            "quality": {"psnr_db_mean": float(np.mean(ps_batch)),
+                        "psnr_db_min": float(np.min(ps_batch))},
+        }
+        bm = statistics.fmean(tv_stream_bytes(w.Z, PARAMS["tv_inner"], True) for w in ws)
+        out["hbm_roofline_model"] = {
+            "bytes_per_voxel_it": bm, "equivalent_GBs": value / world * bm / 1e9,
+            "peak_GBs": peaks["hbm_gbs"], "frac": value / world * bm / 1e9 / peaks["hbm_gbs"],
+            "model": "streaming TV + z prox, one HBM pass per Chambolle step (mean over items)"}
+        print(json.dumps(out), flush=True)
+    batch.close()
+    for plan in plans:
+        plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_tvz(args) -> None:
+    """The single-volume configuration (512 x 512 x 16, 100 iterations) with the
+    same line layout as the default bench."""
     import numpy as np
     import torch
     import torch.distributed as dist
@@ -282,7 +558,7 @@ def run_ours(args) -> None:
 
     w = rank_workload(rank)
     data = synth.generate(w)
-    prm = cs.Params(**PARAMS)
+    prm = cs.Params(**PARAMS_TVZ)
     vox = w.Z * w.H * w.W
     masks_h = torch.from_numpy(data["masks"]).pin_memory()
     b_h = torch.from_numpy(data["b"]).pin_memory()
@@ -319,13 +595,13 @@ def run_ours(args) -> None:
 
     ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    cs.timing_read(DOMINANT, reset=True)
+    cs.timing_read(TVZ_DOMINANT, reset=True)
 
     barrier()
     torch.cuda.synchronize()
     t_wall0 = time.time()
     n0 = cs.launch_count()
-    cs.timing_enable(TIMING_PERIOD)
+    cs.timing_enable(4)
     for k in range(args.steps):
         flush.zero_()
         ev_s[k].record(stream)
@@ -341,7 +617,7 @@ def run_ours(args) -> None:
     clk = clocks.stop() if clocks else None
     step_ms = [ev_s[k].elapsed_time(ev_e[k]) for k in range(args.steps)]
     total_ms = sum(step_ms)
-    n_dom, ms_dom = cs.timing_read(DOMINANT, reset=True)
+    n_dom, ms_dom = cs.timing_read(TVZ_DOMINANT, reset=True)
 
     # end to end through the public API: host inputs in, host result out
     e2e_ms = []
@@ -359,7 +635,7 @@ def run_ours(args) -> None:
     e2e_total = sum(e2e_ms)
 
     total_ms, e2e_total = max_over_ranks([total_ms, e2e_total], world, dev)
-    units = vox * PARAMS["iters"] * args.steps
+    units = vox * PARAMS_TVZ["iters"] * args.steps
     value = job_throughput(units, world, total_ms)
     e2e_value = job_throughput(units, world, e2e_total)
 
@@ -370,27 +646,27 @@ def run_ours(args) -> None:
             avg_s = ms_dom / n_dom / 1e3
             # the dominant kernel's launches per solve: one per iteration, or one
             # for the whole solve; its TV work per launch follows
-            per_step = n_dom * TIMING_PERIOD / args.steps
-            achieved = (PARAMS["iters"] * w.Z * tv_flops_per_launch(w.H, w.W, PARAMS["tv_inner"])
+            per_step = n_dom * 4 / args.steps
+            achieved = (PARAMS_TVZ["iters"] * w.Z * tv_flops_per_launch(w.H, w.W, PARAMS_TVZ["tv_inner"])
                         / per_step / avg_s / 1e12)
             peak = alu_peak_tflops(sm_max)
-            roof = {"bound": "alu", "kernel": DOMINANT, "achieved": achieved, "peak": peak,
-                    "unit": "TFLOP/s", "frac": achieved / peak, "traffic": _traffic(),
+            roof = {"bound": "alu", "kernel": TVZ_DOMINANT, "achieved": achieved, "peak": peak,
+                    "unit": "TFLOP/s", "frac": achieved / peak, "traffic": _traffic(TVZ_DOMINANT, "tvz_512x512x16", TVZ_SOURCES),
                     "avg_launch_us": avg_s * 1e6, "launches_timed": n_dom,
                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
-                    "share_of_step": ms_dom * TIMING_PERIOD / total_ms}
-        cpu = cpu_baseline(data, PARAMS["iters"]) if world == 1 or rank == 0 else None
+                    "share_of_step": ms_dom * 4 / total_ms}
+        cpu = cpu_baseline_tvz(data, PARAMS_TVZ["iters"]) if world == 1 or rank == 0 else None
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded Gaussian-blob volumes, Bernoulli DMD masks)",
-            "config": _config(world), "roofline": roof, "cpu_baseline": cpu,
+            "config": _config_tvz(world), "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": int(masks_h.numel() + b_h.numel() * 4),
                     "d2h_bytes_per_step": int(v_h.numel() * 4)},
             "gpu_launches": int(launches), "clocks": clk,
-            "zsweep_shape": cs.zsweep_shape(w.H, w.W, w.Z, PARAMS["tv_inner"]),
+            "zsweep_shape": cs.zsweep_shape(w.H, w.W, w.Z, PARAMS_TVZ["tv_inner"]),
             "step_ms": [round(x, 3) for x in step_ms],
             "quality": _quality(cs, v_d, data, dev),
         }
@@ -399,7 +675,7 @@ def run_ours(args) -> None:
         # This solver keeps the prox on chip (its kernel roofline is "roofline");
         # the figure says how far the whole step runs ahead of an unfused one.
         peaks = _peaks()
-        bm = tv_stream_bytes(w.Z, PARAMS["tv_inner"], True)
+        bm = tv_stream_bytes(w.Z, PARAMS_TVZ["tv_inner"], True)
         out["hbm_roofline_model"] = {
             "bytes_per_voxel_it": bm, "equivalent_GBs": value / world * bm / 1e9,
             "peak_GBs": peaks["hbm_gbs"], "frac": value / world * bm / 1e9 / peaks["hbm_gbs"],
@@ -458,6 +734,9 @@ def run_secondary(args) -> None:
     name = args.workload
     out = {"workload": name, "steps": args.steps, "warmup": args.warmup}
     peaks = _peaks()
+    if name == "tvz_512x512x16":
+        run_tvz(args)
+        return
     if name in ("tikhonov_1024x1024x32", "tv_1024x1024x32", "bm3d_1024x1024x32",
                 "tv_128x128x8"):
         wk = synth.WORKLOADS["tv_128x128x8" if name == "tv_128x128x8" else "bm3d_1024x1024x32"]
@@ -503,48 +782,6 @@ def run_secondary(args) -> None:
                                "streaming_model_GBs": vox * tv_stream_bytes(wk.Z, 20, False)
                                / (sum(ms) / steps / iters / 1e3) / 1e9}
         plan.close()
-    elif name == "batched_64":
-        import multiprocessing as mp
-
-        rng = np.random.default_rng(4000)
-        sizes = [(int(rng.choice([8, 16, 32])), int(rng.choice([256, 512, 768, 1024])))
-                 for _ in range(64)]
-        specs = [(f"b{i}", Z, S, S, dict(drift=True, mask_p=0.3, peak=50.0, sigma_g=0.02,
-                                           seed=4000 + i, n_blobs=min(2000, synth.blob_count(Z, S, S))))
-                 for i, (Z, S) in enumerate(sizes)]
-        with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 4)) as pool:
-            datas = pool.map(_gen, specs)
-        base = dict(rho=1.0, lam=0.05, gamma=0.2, iters=60, denoiser="tv", tv_inner=20)
-        items, plans = [], []
-        for (Z, S), dd in zip(sizes, datas):
-            plan = cs.Plan(S, S, 1, Z, torch.from_numpy(dd["masks"]).to(dev))
-            items.append((plan, torch.from_numpy(dd["b"]).to(dev),
-                          torch.empty((Z, S, S), dtype=torch.float32, device=dev)))
-        vox = sum(Z * S * S for Z, S in sizes)
-        res = {}
-        cs.set_autotune(1)
-        for storage in ("bf16", "fp32"):
-            batch = cs.Batch(items, cs.Params(storage=storage, **base))
-            ms = _timed(lambda: (batch.run(), batch.wait()), max(1, args.steps // 2), 1, flush)
-            ps = [oracle.psnr(v.double().cpu().numpy(), dd["x"]) for (_, _, v), dd in zip(items, datas)]
-            res[storage] = (sum(ms) / len(ms), ps)
-            batch.close()
-        plain_prm = cs.Params(storage="fp32", **base)
-
-        def plain():
-            for plan, b, v in items:
-                plan.solve(b, plain_prm, v_out=v)
-
-        ms_plain = _timed(plain, 1, 1, flush)
-        ps_plain = [oracle.psnr(v.double().cpu().numpy(), dd["x"]) for (_, _, v), dd in zip(items, datas)]
-        out.update(metric=METRIC, unit=UNIT, items=64, voxels=vox, iterations=60,
-                   value=vox * 60 / (res["bf16"][0] / 1e3),
-                   batched_bf16_ms=res["bf16"][0], batched_fp32_ms=res["fp32"][0],
-                   plain_fp32_ms=sum(ms_plain),
-                   plain_fp32_value=vox * 60 / (sum(ms_plain) / 1e3),
-                   batched_fp32_value=vox * 60 / (res["fp32"][0] / 1e3),
-                   max_dpsnr_bf16_vs_plain=max(abs(a - b) for a, b in zip(res["bf16"][1], ps_plain)),
-                   max_dpsnr_fp32_vs_plain=max(abs(a - b) for a, b in zip(res["fp32"][1], ps_plain)))
     elif name in ("unrolled_b8", "unrolled_b1"):
         # batch 8 with the dual iterates kept (29 GB of workspace); batch 1 with
         # them recomputed (a few hundred MB: the case for full profiler captures)
@@ -668,8 +905,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=None,
-                    help="secondary workload: tikhonov_1024x1024x32, tv_1024x1024x32, "
-                         "bm3d_1024x1024x32, tv_128x128x8, batched_64, unrolled_b8, unrolled_b1, "
+                    help="secondary workload: tvz_512x512x16, tikhonov_1024x1024x32, "
+                         "tv_1024x1024x32, bm3d_1024x1024x32, tv_128x128x8, unrolled_b8, unrolled_b1, "
                          "cr_sweep_256x256x40, tol_caps_512x512x16, wnnm_512x512x16")
     args = ap.parse_args()
     if args.workload:

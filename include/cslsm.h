@@ -195,6 +195,16 @@ cslsm_status cslsm_bm3d_match(const float *img, int Z, int H, int W, int stage, 
 cslsm_status cslsm_bm3d_stage(int stage, const float *noisy, const float *guide, float *out,
                               int Z, int H, int W, float sigma, void *stream);
 
+/* cslsm_bm3d_stage with its decisions exposed, for checking them one by one:
+ * lists (device int32 [Z][nref][16]) and counts ([Z][nref]) receive the
+ * stage's groups as cslsm_bm3d_match gives them, group_stat (device float
+ * [Z][nref]) per group the number of coefficients the hard threshold kept
+ * (stage 1) or the sum of the squared Wiener factors (stage 2), the quantity
+ * each group's aggregation weight is formed from.  Needs H, W >= 8. */
+cslsm_status cslsm_bm3d_stage_groups(int stage, const float *noisy, const float *guide,
+                                     float *out, int Z, int H, int W, float sigma, int *lists,
+                                     int *counts, float *group_stat, void *stream);
+
 /* ---- batched solver --------------------------------------------------------
  * Many independent measurements (each with its own plan: size, slice count,
  * patterns) reconstructed by Algorithm 1 with the TV prior (and the z term

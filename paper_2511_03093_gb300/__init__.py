@@ -115,6 +115,7 @@ def lib() -> ctypes.CDLL:
         "cslsm_ssim3d": [P, P, I, I, I, P, P],
         "cslsm_bm3d_match": [P, I, I, I, I, P, P, P],
         "cslsm_bm3d_stage": [I, P, P, P, I, I, I, F, P],
+        "cslsm_bm3d_stage_groups": [I, P, P, P, I, I, I, F, P, P, P, P],
     }
     for name, args in sigs.items():
         fn = getattr(L, name)
@@ -359,6 +360,30 @@ def bm3d_stage(stage: int, noisy: torch.Tensor, sigma: float, guide: torch.Tenso
                                   _dev(out, "out", torch.float32, (Z, H, W)), Z, H, W,
                                   float(sigma), _stream(stream)), "cslsm_bm3d_stage")
     return out
+
+
+def bm3d_stage_groups(stage: int, noisy: torch.Tensor, sigma: float,
+                      guide: torch.Tensor | None = None, stream=None):
+    """One BM3D stage on each slice with its decisions (cslsm_bm3d_stage_groups):
+    (out [Z,H,W], lists int32 [Z,nref,16], counts int32 [Z,nref], stat float32
+    [Z,nref]: kept coefficients per group (stage 1) or sum of squared Wiener factors)."""
+    if noisy.dim() == 2:
+        noisy = noisy[None]
+        guide = guide[None] if guide is not None else None
+    Z, H, W = noisy.shape
+    nref = lib().cslsm_bm3d_num_refs(H, W)
+    out = torch.empty_like(noisy)
+    lists = torch.empty((Z, nref, 16), dtype=torch.int32, device=noisy.device)
+    counts = torch.empty((Z, nref), dtype=torch.int32, device=noisy.device)
+    stat = torch.empty((Z, nref), dtype=torch.float32, device=noisy.device)
+    gp = _dev(guide, "guide", torch.float32, (Z, H, W)) if guide is not None else None
+    _check(lib().cslsm_bm3d_stage_groups(int(stage), _dev(noisy, "noisy", torch.float32), gp,
+                                         _dev(out, "out", torch.float32, (Z, H, W)), Z, H, W,
+                                         float(sigma), ctypes.c_void_p(lists.data_ptr()),
+                                         ctypes.c_void_p(counts.data_ptr()),
+                                         ctypes.c_void_p(stat.data_ptr()), _stream(stream)),
+           "cslsm_bm3d_stage_groups")
+    return out, lists, counts, stat
 
 
 def set_autotune(mode: int) -> None:

@@ -845,6 +845,35 @@ cslsm_status cslsm_bm3d_stage(int stage, const float *noisy, const float *guide,
     return st;
 }
 
+cslsm_status cslsm_bm3d_stage_groups(int stage, const float *noisy, const float *guide,
+                                     float *out, int Z, int H, int W, float sigma, int *lists,
+                                     int *counts, float *group_stat, void *stream)
+{
+    CHECK_ARG(noisy != nullptr && out != nullptr, "noisy and out must be non-NULL");
+    CHECK_ARG(lists != nullptr && counts != nullptr && group_stat != nullptr,
+              "lists, counts and group_stat must be non-NULL");
+    CHECK_ARG(stage == 1 || (stage == 2 && guide != nullptr),
+              "stage must be 1, or 2 with a guide");
+    CHECK_ARG(Z >= 1 && H >= 8 && W >= 8, "need Z >= 1 and H, W >= 8");
+    CHECK_ARG((long long)Z * H * W < (1ll << 31), "Z*H*W must be < 2^31");
+    CHECK_ARG(std::isfinite(sigma) && sigma > 0.f, "sigma must be > 0");
+    cudaStream_t s = as_stream(stream);
+    const size_t need = bm3d_workspace_bytes(Z, H, W);
+    void *ws = nullptr;
+    CSLSM_CUDA(cudaMallocAsync(&ws, need, s));
+    cudaError_t e = cudaMemsetAsync(ws, 0, need, s);
+    cslsm_status st = CSLSM_OK;
+    if (e != cudaSuccess) {
+        set_error("cudaMemsetAsync: %s", cudaGetErrorString(e));
+        st = CSLSM_ERR_CUDA;
+    } else {
+        st = bm3d_stage_only(stage, noisy, guide, out, Z, H, W, sigma, ws, s, lists, counts,
+                             group_stat);
+    }
+    cudaFreeAsync(ws, s);
+    return st;
+}
+
 cslsm_status cslsm_psnr(const float *x, const float *ref, size_t n, double *out, void *stream)
 {
     CHECK_ARG(x != nullptr && ref != nullptr && out != nullptr, "x, ref, out must be non-NULL");

@@ -194,8 +194,12 @@ size_t bm3d_workspace_bytes(int nslices, int H, int W);
 cslsm_status bm3d_slices(const Bm3dSlices &b, void *ws, cudaStream_t s);
 // WNNM u-step on the same groups and workspace (hard-stage matching, one pass).
 cslsm_status wnnm_slices(const Bm3dSlices &b, void *ws, cudaStream_t s);
+// One stage; when lists / counts / stat are not null they receive the stage's
+// match lists [ns][nref][16], group sizes [ns][nref] and per-group statistic
+// (hard: kept coefficients; Wiener: sum of squared shrinkage factors).
 cslsm_status bm3d_stage_only(int stage, const float *noisy, const float *guide, float *out,
-                             int nslices, int H, int W, float sigma, void *ws, cudaStream_t s);
+                             int nslices, int H, int W, float sigma, void *ws, cudaStream_t s,
+                             int *lists = nullptr, int *counts = nullptr, float *stat = nullptr);
 cslsm_status bm3d_match_only(const float *img, int nslices, int H, int W, int stage, int *lists,
                              int *counts, void *ws, cudaStream_t s);
 

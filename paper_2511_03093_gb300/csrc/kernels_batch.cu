@@ -65,7 +65,7 @@ struct BItem {
     float *pbuf;  // [2 parities][2 components][slots][H][W], slots = 1 (gamma > 0) or Z
     int wstride;
     int H, W, N, R, Z;
-    int hh, TH, TW, tiles_x, tiles;
+    int hh, hc, TH, TW, tiles_x, tiles;  // row / column halo, tile rows / columns
     int units_x;
     long long units_lvl;  // TV units per level
     long long units_iter;
@@ -158,27 +158,28 @@ __device__ void tv_unit(const BItem &it, const BDesc &D, int n, int j, int tile,
 {
     constexpr unsigned FULL = 0xffffffffu;
     constexpr int B = kBW, RPW = kBR, NR = kBR + 1, RH = kBRH;
-    const int H = it.H, W = it.W, hh = it.hh, TH = it.TH, TW = it.TW;
+    const int H = it.H, W = it.W, hh = it.hh, hc = it.hc, TH = it.TH, TW = it.TW;
     const int bx = tile % it.tiles_x, by = tile / it.tiles_x;
-    const int gi0 = by * TH - hh, gj0 = bx * TW - hh;
+    const int gi0 = by * TH - hh, gj0 = bx * TW - hc;  // gj0 even: a lane's columns pair up
     const size_t HW = (size_t)H * W;
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     const int j0 = 2 * lane, r0 = 1 + wp * RPW, gc = gj0 + j0;
     const float mc0 = (gc >= 0 && gc < W - 1) ? 1.f : 0.f;
     const float mc1 = (gc + 1 >= 0 && gc + 1 < W - 1) ? 1.f : 0.f;
     const bool inc[2] = {gc >= 0 && gc < W, gc + 1 >= 0 && gc + 1 < W};
-    const bool ownc[2] = {inc[0] && j0 >= hh && j0 < hh + TW,
-                          inc[1] && j0 + 1 >= hh && j0 + 1 < hh + TW};
+    const bool ownc[2] = {inc[0] && j0 >= hc && j0 < hc + TW,
+                          inc[1] && j0 + 1 >= hc && j0 + 1 < hc + TW};
     const bool interior = gi0 >= 0 && gi0 + RH < H && gj0 >= 0 && gj0 + kBPW < W;
     const unsigned Hm1 = (unsigned)(H - 1);
     float mr[RPW];
     int off[NR];
-    unsigned inm = 0, ownm = 0;
+    unsigned inm = 0, ownm = 0, pairm = 0;  // pairm: both columns in, pair aligned
 #pragma unroll
     for (int i = 0; i < NR; ++i) {
         const int gi = gi0 + r0 + i;
         const bool inr = gi >= 0 && gi < H;
         off[i] = gi * W + gc;
+        if (inr && inc[0] && inc[1] && !(off[i] & 1)) pairm |= 1u << i;
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
             if (inr && inc[c]) inm |= 1u << (2 * i + c);
@@ -199,14 +200,31 @@ __device__ void tv_unit(const BItem &it, const BDesc &D, int n, int j, int tile,
     {
         float gv[2 * NR];
 #pragma unroll
-        for (int q = 0; q < 2 * NR; ++q) {
-            gv[q] = 0.f;
-            if (inm & (1u << q)) {
-                const size_t o = (size_t)(off[q >> 1] + (q & 1));
-                const float wv = ld_l2<S>(wn + o);
-                gv[q] = gam > 0.f ? (rho * wv + gam * (ld_l2<S>(um + o) + ld_l2<S>(up + o))) *
-                                        inv_rho2g
-                                  : wv;
+        if (pairm == (1u << NR) - 1) {  // every row: one load per field for both columns
+#pragma unroll
+            for (int i = 0; i < NR; ++i) {
+                const size_t o = (size_t)off[i];
+                const float2 w2 = ld2_l2<S>(wn + o);
+                if (gam > 0.f) {
+                    const float2 a2 = ld2_l2<S>(um + o), b2 = ld2_l2<S>(up + o);
+                    gv[2 * i] = (rho * w2.x + gam * (a2.x + b2.x)) * inv_rho2g;
+                    gv[2 * i + 1] = (rho * w2.y + gam * (a2.y + b2.y)) * inv_rho2g;
+                } else {
+                    gv[2 * i] = w2.x;
+                    gv[2 * i + 1] = w2.y;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 2 * NR; ++q) {
+                gv[q] = 0.f;
+                if (inm & (1u << q)) {
+                    const size_t o = (size_t)(off[q >> 1] + (q & 1));
+                    const float wv = ld_l2<S>(wn + o);
+                    gv[q] = gam > 0.f
+                                ? (rho * wv + gam * (ld_l2<S>(um + o) + ld_l2<S>(up + o))) * inv_rho2g
+                                : wv;
+                }
             }
         }
 #pragma unroll
@@ -224,6 +242,13 @@ __device__ void tv_unit(const BItem &it, const BDesc &D, int n, int j, int tile,
     if (j > 0) {
         const float *P1 = it.pbuf + ((size_t)((j - 1) & 1) * 2 * Zp + slot) * HW;
         const float *P2 = P1 + (size_t)Zp * HW;
+        if (pairm == (1u << NR) - 1) {
+#pragma unroll
+            for (int i = 0; i < RPW; ++i) {
+                p1[i] = __ldcg(reinterpret_cast<const float2 *>(P1 + off[i]));
+                p2[i] = __ldcg(reinterpret_cast<const float2 *>(P2 + off[i]));
+            }
+        } else {
 #pragma unroll
         for (int i = 0; i < RPW; ++i) {
             if (inm & (1u << (2 * i))) {
@@ -234,6 +259,7 @@ __device__ void tv_unit(const BItem &it, const BDesc &D, int n, int j, int tile,
                 p1[i].y = __ldcg(P1 + off[i] + 1);
                 p2[i].y = __ldcg(P2 + off[i] + 1);
             }
+        }
         }
         if (wp == 0 || wp == B - 1) {  // frozen rows 0 and RH - 1 of the region
             const int gi = gi0 + (wp == 0 ? 0 : RH - 1);
@@ -416,7 +442,7 @@ cslsm_status batch_build(const BatchSpec &spec, BatchRun &run)
     const int k = T > 0 ? std::max(1, std::min(spec.k, T)) : 0;
     const int P = T > 0 ? (T + k - 1) / k : 1;
     const int hh = k + 1;
-    if (kBRH - 2 * hh < 1 || kBPW - 2 * hh < 1) {
+    if (kBRH - 2 * hh < 1 || kBPW - 2 * (hh + (hh & 1)) < 2) {
         set_error("batched TV: %d steps per phase leave no tile", k);
         return CSLSM_ERR_UNSUPPORTED;
     }
@@ -440,8 +466,9 @@ cslsm_status batch_build(const BatchSpec &spec, BatchRun &run)
         b.R = s.R;
         b.Z = s.N * s.R;
         b.hh = hh;
+        b.hc = hh + (hh & 1);  // even column halo: regions start on even columns
         b.TH = kBRH - 2 * hh;
-        b.TW = kBPW - 2 * hh;
+        b.TW = kBPW - 2 * b.hc;
         b.tiles_x = (s.W + b.TW - 1) / b.TW;
         b.tiles = b.tiles_x * ((s.H + b.TH - 1) / b.TH);
         b.units_x = (s.H * s.W + kBNT - 1) / kBNT;

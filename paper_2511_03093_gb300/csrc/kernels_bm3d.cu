@@ -458,6 +458,7 @@ struct FilterArgs {
     int H, W, ns;
     float sigma;
     const int *stop;      // tolerance-stopped solve: skip (or nullptr)
+    float *stat;          // [ns][nref] per-group kept count / sum W^2, or nullptr
 };
 
 // Persistent: each CTA takes 8 x 8 blocks of references (one slice each) in
@@ -591,6 +592,7 @@ __global__ void __launch_bounds__(kTcWarps * 32, 2) bm3d_filter_tc_kernel(const 
             for (int o = 16; o > 0; o >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
             const float weight = kWiener ? (wsum > 0.f ? 1.f / (s2 * wsum) : 1.f / s2)
                                          : 1.f / (s2 * fmaxf(wsum, 1.f));
+            if (a.stat && lane == 0) a.stat[gi] = wsum;
             float o[8][4];
             inverse_3d(tb, z, lgL, lane, o);
             const float back = pow2f(-e - 8);
@@ -1097,9 +1099,10 @@ cslsm_status launch_filter_tc(const FilterArgs &a, cudaStream_t s)
 }
 
 cslsm_status filter(int stage, const float *noisy, const float *guide, const Ws &w, int ns,
-                    int H, int W, float sigma, cudaStream_t s, const int *stop = nullptr)
+                    int H, int W, float sigma, cudaStream_t s, const int *stop = nullptr,
+                    float *stat = nullptr)
 {
-    FilterArgs a{noisy, guide, w.lists, w.counts, w.num, w.den, H, W, ns, sigma, stop};
+    FilterArgs a{noisy, guide, w.lists, w.counts, w.num, w.den, H, W, ns, sigma, stop, stat};
     LaunchScope ls(K_BM3D_FILTER, s);
     cslsm_status e = stage == 1 ? launch_filter_tc<false>(a, s) : launch_filter_tc<true>(a, s);
     if (e) return e;
@@ -1235,7 +1238,8 @@ cslsm_status bm3d_slices(const Bm3dSlices &b, void *ws, cudaStream_t s)
 }
 
 cslsm_status bm3d_stage_only(int stage, const float *noisy, const float *guide, float *out,
-                             int ns, int H, int W, float sigma, void *ws, cudaStream_t s)
+                             int ns, int H, int W, float sigma, void *ws, cudaStream_t s,
+                             int *lists, int *counts, float *stat)
 {
     cslsm_status e = upload_constants();
     if (e) return e;
@@ -1250,7 +1254,13 @@ cslsm_status bm3d_stage_only(int stage, const float *noisy, const float *guide, 
         return CSLSM_OK;
     }
     if ((e = match(w.codes, ns, H, W, stage, w.lists, w.counts, s))) return e;
-    if ((e = filter(stage, noisy, guide, w, ns, H, W, sigma, s))) return e;
+    const size_t nref = (size_t)ns * n_refs(H) * n_refs(W);
+    if (lists)
+        CSLSM_CUDA(cudaMemcpyAsync(lists, w.lists, sizeof(int) * nref * kMaxGroup,
+                                   cudaMemcpyDeviceToDevice, s));
+    if (counts)
+        CSLSM_CUDA(cudaMemcpyAsync(counts, w.counts, sizeof(int) * nref, cudaMemcpyDeviceToDevice, s));
+    if ((e = filter(stage, noisy, guide, w, ns, H, W, sigma, s, nullptr, stat))) return e;
     return finish_stage<float>(w, out, nullptr, nullptr, nullptr, ns, H, W, s);
 }
 

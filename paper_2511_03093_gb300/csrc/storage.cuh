@@ -47,6 +47,28 @@ __device__ __forceinline__ float ld_l2<__half>(const __half *p)
     return __half2float(__ldcg(p));
 }
 
+// Two consecutive elements, L2 only (8-byte aligned for float, 4-byte for
+// 16-bit types).
+template <typename S>
+__device__ __forceinline__ float2 ld2_l2(const S *p);
+template <>
+__device__ __forceinline__ float2 ld2_l2<float>(const float *p)
+{
+    return __ldcg(reinterpret_cast<const float2 *>(p));
+}
+template <>
+__device__ __forceinline__ float2 ld2_l2<__nv_bfloat16>(const __nv_bfloat16 *p)
+{
+    const unsigned r = __ldcg(reinterpret_cast<const unsigned *>(p));
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&r));
+}
+template <>
+__device__ __forceinline__ float2 ld2_l2<__half>(const __half *p)
+{
+    const unsigned r = __ldcg(reinterpret_cast<const unsigned *>(p));
+    return __half22float2(*reinterpret_cast<const __half2 *>(&r));
+}
+
 template <typename S>
 __device__ __forceinline__ void st(S *p, float v);
 template <>

@@ -26,6 +26,7 @@ import numpy as np
 __all__ = [
     "Workload",
     "WORKLOADS",
+    "batch_workloads",
     "blob_count",
     "make_volume",
     "make_masks",
@@ -74,6 +75,20 @@ WORKLOADS: dict[str, Workload] = {
     "bm3d_1024x1024x32": Workload("bm3d_1024x1024x32", 32, 1024, 1024, mask_p=0.5,
                                   peak=200.0, sigma_g=0.01, seed=1003),
 }
+
+
+def batch_workloads(n: int = 64, seed: int = 4000, max_blobs: int = 2000) -> list[Workload]:
+    """The batch of independent measurements: item i has H = W drawn uniformly
+    from {256, 512, 768, 1024} and Z from {8, 16, 32} (one numpy stream seeded
+    with `seed`, Z first), drifting blobs (at most `max_blobs` per item, to keep
+    the host-side generation of the 64-item batch to seconds), Bernoulli(0.3)
+    patterns, Poisson peak 50 + Gaussian sigma 0.02, and seed `seed` + i."""
+    rng = np.random.default_rng(seed)
+    sizes = [(int(rng.choice([8, 16, 32])), int(rng.choice([256, 512, 768, 1024])))
+             for _ in range(n)]
+    return [Workload(f"b{i}", Z, S, S, drift=True, mask_p=0.3, peak=50.0, sigma_g=0.02,
+                     seed=seed + i, n_blobs=min(max_blobs, blob_count(Z, S, S)))
+            for i, (Z, S) in enumerate(sizes)]
 
 
 def blob_count(Z: int, H: int, W: int) -> int:

@@ -39,3 +39,17 @@ def test_streaming_byte_model():
     # x-update 12.125 + 4 / R, first pass 12, 19 later passes of 20, finalize 20, z term 8
     assert bench.tv_stream_bytes(16, 20, True) == 12.125 + 0.25 + 12 + 19 * 20 + 20 + 8
     assert bench.tv_stream_bytes(32, 20, False) == 424.25
+
+
+def test_oracle_sample_is_stratified_by_size():
+    ws = bench.rank_workloads(0)
+    assert len(ws) == 64 and sum(w.Z * w.H * w.W for w in ws) == 613941248
+    idx = bench.oracle_sample(ws)
+    assert len(set(idx)) == 8
+    sizes = sorted(w.Z * w.H * w.W for w in ws)
+    got = [ws[i].Z * ws[i].H * ws[i].W for i in idx]
+    assert got == sorted(got)
+    for k, v in enumerate(got):  # one item from each eighth of the size order
+        assert sizes[8 * k] <= v <= sizes[8 * k + 7]
+    # replicas draw different batches
+    assert [w.seed for w in bench.rank_workloads(1)] != [w.seed for w in ws]

@@ -1,17 +1,19 @@
 """BM3D u-step: CUDA path vs the FP64 oracle through the C ABI.
 
-Bars: match lists bit-exact (integer work on identical float32 inputs); the
-Wiener stage on an identical basic estimate within relative L2 1e-5 (no
-discontinuous decision); the hard stage and the whole denoiser, whose hard
-threshold can flip on 1-ulp differences between FP32 and FP64 coefficients,
-within relative L2 1e-4 and with at most 0.1 % of pixels off by more than 1e-4;
-full ADMM runs with BM3D within 0.05 dB PSNR of the oracle.
+Bars: match lists bit-exact (integer work on identical float32 inputs); every
+stage element-wise within relative L2 1e-5 of the oracle outside the footprints
+of the groups whose decisions flipped (a hard-threshold decision on a
+coefficient a few FP32 roundings from 2.7 sigma, found by comparing each
+group's kept-coefficient count with the oracle's; a Wiener group whose match
+list or guide differs), with the flipped groups counted and held to a small
+fraction; full ADMM runs with BM3D within 0.05 dB PSNR of the oracle.
 """
 import numpy as np
 import pytest
 
 import oracle
 import synth
+from tests import bm3d_check as bc
 from tests.gpu_util import DPSNR, REL_ITER, rel_l2, to_dev, to_np
 
 pytestmark = pytest.mark.gpu
@@ -85,17 +87,23 @@ def test_wiener_stage_on_identical_guide(cs, Z, H, W):
     assert rel_l2(out, ref) <= REL_ITER
 
 
-def _close_with_flips(out, ref):
-    diff = np.abs(out - ref)
-    return rel_l2(out, ref) <= 1e-4 and np.mean(diff > 1e-4) <= 1e-3
+def _flip_bounds(chk, max_frac=0.01):
+    """Flips are rare (coefficients within FP32 rounding of the threshold): a
+    systematic error would flip many groups and leave few pixels to compare."""
+    assert chk.flipped <= max(2, max_frac * chk.groups), (chk.flipped, chk.groups)
+    assert chk.kept_pixels >= 0.5 * chk.pixels, (chk.kept_pixels, chk.pixels)
 
 
-@pytest.mark.parametrize("Z,H,W", [(2, 37, 53), (1, 96, 96)])
+@pytest.mark.parametrize("Z,H,W", [(2, 37, 53), (1, 96, 96), (1, 130, 70)])
 def test_hard_stage(cs, Z, H, W):
     noisy = _blobs(11 + H, Z, H, W)
-    out = to_np(cs.bm3d_stage(1, to_dev(noisy), 0.04))
-    ref = np.stack([oracle.bm3d_stage(noisy[z], 0.04) for z in range(Z)])
-    assert _close_with_flips(out, ref), (rel_l2(out, ref), np.mean(np.abs(out - ref) > 1e-4))
+    chk = bc.Check()
+    out, ref, keep = bc.hard_stage(cs, noisy, 0.04, chk)
+    assert bc.rel_on(out, ref, keep) <= REL_ITER, (bc.rel_on(out, ref, keep), chk.flipped)
+    _flip_bounds(chk)
+    # the plain stage entry point gives the same result as the diagnostic one
+    np.testing.assert_allclose(to_np(cs.bm3d_stage(1, to_dev(noisy), 0.04)), out, rtol=0,
+                               atol=1e-6)
 
 
 def test_hard_stage_zero_threshold_limit(cs):
@@ -109,15 +117,23 @@ def test_hard_stage_zero_threshold_limit(cs):
 def test_denoise_bm3d(cs, Z, H, W):
     noisy = _blobs(5 + W, Z, H, W)
     out = to_np(cs.denoise(to_dev(noisy), cs.Params(denoiser="bm3d", bm3d_sigma=0.04)))
-    ref = oracle.bm3d(noisy, 0.04)
-    assert rel_l2(out, ref) <= 1e-3
+    chk = bc.Check()
+    ref, keep = bc.denoise(cs, noisy, 0.04, chk)
+    assert bc.rel_on(out, ref, keep) <= REL_ITER, (bc.rel_on(out, ref, keep), chk.flipped)
+    _flip_bounds(chk)
     clean = synth.generate(synth.Workload("b", Z, H, W, seed=5 + W, peak=None,
                                           n_blobs=max(4, Z * H * W // 300)))["x"]
-    assert abs(oracle.psnr(out, clean) - oracle.psnr(ref, clean)) <= DPSNR
+    assert abs(oracle.psnr(out, clean) - oracle.psnr(oracle.bm3d(noisy, 0.04), clean)) <= DPSNR
 
 
-@pytest.mark.parametrize("gamma", [0.0, 0.2])
+@pytest.mark.parametrize("gamma", [0.0, 0.5])
 def test_one_iteration_bm3d(cs, gamma):
+    """One ADMM iteration (Algorithm 1) with the BM3D u-step from a given state.
+    v against the oracle; every slice's u against the oracle's BM3D of the prox
+    input the sweep formed for it (from the GPU's own newer neighbour, so a flip
+    in one slice is not carried into the check of the next), element-wise
+    outside flipped groups.  rho = 1, gamma = 0.5 make the prox input's FP32
+    arithmetic exact to restate: g = (w + (u_prev + u_next) / 2) / 2."""
     import torch
 
     Z, H, W = 4, 40, 48
@@ -132,21 +148,24 @@ def test_one_iteration_bm3d(cs, gamma):
     u, d = to_dev(u0), to_dev(d0)
     v = plan.solve(to_dev(b), prm, u=u, d=d, init_user=True)
     torch.cuda.synchronize()
-    v_r, u_r, d_r, _ = oracle.admm(b, masks, Z, rho=1.0, lam=0.0, gamma=gamma, iters=1,
-                                   denoiser="bm3d", bm3d_sigma=0.04, u0=u0, d0=d0)
-    assert rel_l2(to_np(v), v_r) <= REL_ITER
-    ug = to_np(u)
-    if gamma == 0.0:
-        assert _close_with_flips(ug, u_r)
-    else:
-        # The first slice of the sweep sees the same inputs as the oracle up to
-        # rounding.  Later slices take the previous slice's output as input, and
-        # a hard-threshold or matching decision flipped by one FP32 rounding
-        # changes whole groups (up to 27 pixels away) that the next slice then
-        # sees: the sweep spreads such local changes, so the later slices are
-        # held to the volume-level bar only.
-        assert _close_with_flips(ug[0], u_r[0])
-        assert rel_l2(ug, u_r) <= 1e-2, rel_l2(ug, u_r)
+    v_r, *_ = oracle.admm(b, masks, Z, rho=1.0, lam=0.0, gamma=gamma, iters=1,
+                          denoiser="bm3d", bm3d_sigma=0.04, u0=u0, d0=d0)
+    vg = to_np(v).astype(np.float32)
+    assert rel_l2(vg, v_r) <= REL_ITER
+    ug, dg = to_np(u).astype(np.float32), to_np(d).astype(np.float32)
+    w = vg + d0  # the workspace w = v + d the x-update wrote (FP32)
+    np.testing.assert_array_equal(dg, w - ug)  # dual update d = w - u
+    chk = bc.Check()
+    for n in range(Z):  # sweep order: slice n sees u_{n-1} new and u_{n+1} old
+        if gamma > 0.0:
+            um = ug[n - 1] if n > 0 else u0[Z - 1]
+            up = u0[n + 1] if n < Z - 1 else ug[0]
+            g = ((w[n] + np.float32(0.5) * (um + up)) * np.float32(0.5)).astype(np.float32)
+        else:
+            g = w[n]
+        ref, keep = bc.denoise(cs, g[None], 0.04, chk)
+        assert bc.rel_on(ug[n][None], ref, keep) <= REL_ITER, (n, chk.flipped)
+    _flip_bounds(chk)
     plan.close()
 
 
