@@ -782,6 +782,25 @@ def run_secondary(args) -> None:
                                "streaming_model_GBs": vox * tv_stream_bytes(wk.Z, 20, False)
                                / (sum(ms) / steps / iters / 1e3) / 1e9}
         plan.close()
+    elif name == "batched_8x6":
+        # a small case of the batched solver for profiler captures: the batch's
+        # stratified 8-item sample (77 M voxels), 6 iterations, BF16 state
+        ws = rank_workloads(0)
+        idx = oracle_sample(ws)
+        sub = [ws[i] for i in idx]
+        datas = _gen_items(sub)
+        items = []
+        for w, d in zip(sub, datas):
+            plan = cs.Plan(w.H, w.W, 1, w.Z, torch.from_numpy(d["masks"]).to(dev))
+            items.append((plan, torch.from_numpy(d["b"]).to(dev),
+                          torch.empty((w.Z, w.H, w.W), dtype=torch.float32, device=dev)))
+        iters = 6
+        batch = cs.Batch(items, cs.Params(**dict(PARAMS, iters=iters)))
+        ms = _timed(lambda: (batch.run(), batch.wait()), max(1, args.steps), args.warmup, flush)
+        vox = sum(w.Z * w.H * w.W for w in sub)
+        out.update(metric=METRIC, unit=UNIT, value=vox * iters / (sum(ms) / len(ms) / 1e3),
+                   ms_per_step=sum(ms) / len(ms), iterations=iters, items=idx, voxels=vox)
+        batch.close()
     elif name in ("unrolled_b8", "unrolled_b1"):
         # batch 8 with the dual iterates kept (29 GB of workspace); batch 1 with
         # them recomputed (a few hundred MB: the case for full profiler captures)
@@ -905,7 +924,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=None,
-                    help="secondary workload: tvz_512x512x16, tikhonov_1024x1024x32, "
+                    help="secondary workload: tvz_512x512x16, batched_8x6, tikhonov_1024x1024x32, "
                          "tv_1024x1024x32, bm3d_1024x1024x32, tv_128x128x8, unrolled_b8, unrolled_b1, "
                          "cr_sweep_256x256x40, tol_caps_512x512x16, wnnm_512x512x16")
     args = ap.parse_args()
