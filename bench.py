@@ -45,7 +45,7 @@ METRIC = "PnP-ADMM voxel-iterations/s"
 UNIT = "voxel-it/s"
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 DOMINANT = "batch_persistent"  # one launch = the whole 60-iteration batch
-DOMINANT_SOURCES = ("kernels_batch.cu", "tv_body.cuh")
+DOMINANT_SOURCES = ("kernels_batch.cu", "tv_body.cuh", "storage.cuh")
 TVZ_DOMINANT = "tvz_sweep"  # the single-volume configuration's dominant kernel
 TVZ_SOURCES = ("kernels_tvz.cu", "tv_body.cuh")
 TIMING_PERIOD = 1  # every launch of each kernel timed with CUDA events
@@ -737,13 +737,15 @@ def run_secondary(args) -> None:
     if name == "tvz_512x512x16":
         run_tvz(args)
         return
-    if name in ("tikhonov_1024x1024x32", "tv_1024x1024x32", "bm3d_1024x1024x32",
-                "tv_128x128x8"):
+    if name in ("tikhonov_1024x1024x32", "tikhonovz_1024x1024x32", "tv_1024x1024x32",
+                "bm3d_1024x1024x32", "tv_128x128x8"):
         wk = synth.WORKLOADS["tv_128x128x8" if name == "tv_128x128x8" else "bm3d_1024x1024x32"]
         data = synth.generate(wk)
         den = name.split("_")[0]
+        gam = 0.2 if den == "tikhonovz" else 0.0  # Tikhonov with the z term (Sec. III-C)
+        den = "tikhonov" if den == "tikhonovz" else den
         iters = 50 if name == "tv_128x128x8" else 30
-        prm = cs.Params(rho=1.0, lam=0.0 if den == "bm3d" else 0.05, gamma=0.0, iters=iters,
+        prm = cs.Params(rho=1.0, lam=0.0 if den == "bm3d" else 0.05, gamma=gam, iters=iters,
                         denoiser=den, tv_inner=20, bm3d_sigma=0.05)
         plan = cs.Plan(wk.H, wk.W, 1, wk.Z, torch.from_numpy(data["masks"]).to(dev))
         b = torch.from_numpy(data["b"]).to(dev)
@@ -925,6 +927,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=None,
                     help="secondary workload: tvz_512x512x16, batched_8x6, tikhonov_1024x1024x32, "
+                         "tikhonovz_1024x1024x32, "
                          "tv_1024x1024x32, bm3d_1024x1024x32, tv_128x128x8, unrolled_b8, unrolled_b1, "
                          "cr_sweep_256x256x40, tol_caps_512x512x16, wnnm_512x512x16")
     args = ap.parse_args()

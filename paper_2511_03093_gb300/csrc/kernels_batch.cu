@@ -144,7 +144,7 @@ __device__ void xupdate_unit(const BItem &it, int unit, float rho, bool last)
             const float dr = ld_l2<S>(d + o);
             const float g = ld_l2<S>(u + o) - dr;
             const float v = ((word >> r) & 1u) ? g + e : g;
-            st<S>(w + o, v + dr);
+            st<S>(w + o, keep<S>(v + dr, o, kKeyW));
             if (last) it.v_out[o] = v;
         }
     }
@@ -337,8 +337,10 @@ __device__ void tv_unit(const BItem &it, const BDesc &D, int n, int j, int tile,
             for (int c = 0; c < 2; ++c) {
                 if (!(ownm & (1u << (2 * i + c)))) continue;
                 const size_t o = (size_t)off[i] + c;
-                st<S>(un + o, uu[c]);
-                st<S>(dn + o, wv[i][c] - rnd<S>(uu[c]));
+                const size_t vi = (size_t)n * HW + o;
+                const float ur = keep<S>(uu[c], vi, kKeyU);
+                st<S>(un + o, ur);
+                st<S>(dn + o, keep<S>(wv[i][c] - ur, vi, kKeyD));
             }
         }
     }

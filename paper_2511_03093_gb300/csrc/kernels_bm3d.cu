@@ -833,8 +833,9 @@ bm3d_finish_wimg_kernel(double *__restrict__ num, const double *__restrict__ wim
     const size_t i = base + (size_t)y * W + x;
     const float v = (float)(num[i] / (double)den);
     num[i] = 0.0;
-    st<S>(out + i, v);
-    if (dual) st<S>(dual + i, ld<S>(w + i) - rnd<S>(v));
+    const float ur = keep<S>(v, i, kKeyU);
+    st<S>(out + i, ur);
+    if (dual) st<S>(dual + i, keep<S>(ld<S>(w + i) - ur, i, kKeyD));
     if (codes) {
         const float rr = rintf(__fmul_rn(v, 255.f));
         codes[i] = (uint8_t)(rr < 0.f ? 0.f : (rr > 255.f ? 255.f : rr));
@@ -861,8 +862,9 @@ __global__ void bm3d_finish_kernel(double *__restrict__ num, double *__restrict_
         } else {
             v = (float)num[i];
         }
-        st<S>(out + i, v);
-        if (dual) st<S>(dual + i, ld<S>(w + i) - rnd<S>(v));
+        const float ur = keep<S>(v, (size_t)i, kKeyU);
+        st<S>(out + i, ur);
+        if (dual) st<S>(dual + i, keep<S>(ld<S>(w + i) - ur, (size_t)i, kKeyD));
         if (codes) {
             const float r = rintf(__fmul_rn(v, 255.f));
             codes[i] = (uint8_t)(r < 0.f ? 0.f : (r > 255.f ? 255.f : r));
@@ -879,8 +881,9 @@ __global__ void bm3d_copy_kernel(const float *__restrict__ g, S *__restrict__ ou
     if (stop && *stop) return;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
          i += (long long)gridDim.x * blockDim.x) {
-        st<S>(out + i, g[i]);
-        if (dual) st<S>(dual + i, ld<S>(w + i) - rnd<S>(g[i]));
+        const float ur = keep<S>(g[i], (size_t)i, kKeyU);
+        st<S>(out + i, ur);
+        if (dual) st<S>(dual + i, keep<S>(ld<S>(w + i) - ur, (size_t)i, kKeyD));
     }
 }
 

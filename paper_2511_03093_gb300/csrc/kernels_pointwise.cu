@@ -123,7 +123,7 @@ xupdate_w_kernel(const S *__restrict__ u, const S *__restrict__ d,
             if (r < R) {
                 const int o = base + r * HW;
                 const float v = bit(word, r) ? g[r] + e : g[r];
-                st<S>(w + o, v + dr[r]);
+                st<S>(w + o, keep<S>(v + dr[r], (size_t)o, kKeyW));
                 if (v_out) v_out[o] = v;
                 if (vprev) {
                     const double vp = vprev[o];
@@ -194,14 +194,14 @@ tikhonov_iter_kernel(S *__restrict__ u, S *__restrict__ d, const float *__restri
                         if (n == Z - 1) next = first_new;
                         else if (r + 1 < R) next = ur[r + 1 < RMAX ? r + 1 : r];
                         else next = ld<S>(u + o + HW);  // next shot's first plane, still old
-                        un = rnd<S>((rho * w + gam * (prev + next)) / den);
+                        un = keep<S>((rho * w + gam * (prev + next)) / den, (size_t)o, kKeyU);
                         prev = un;
                         if (n == 0) first_new = un;
                     } else {
-                        un = rho * w / den;
+                        un = keep<S>(rho * w / den, (size_t)o, kKeyU);
                     }
                     st<S>(u + o, un);
-                    st<S>(d + o, w - un);
+                    st<S>(d + o, keep<S>(w - un, (size_t)o, kKeyD));
                     if (v_out) v_out[o] = v;
                     if (vprev) {
                         const double vp = vprev[o];
@@ -267,12 +267,13 @@ tikhonov_iter_v2_kernel(S *__restrict__ u, S *__restrict__ d, const float *__res
                 if (n == Z - 1) nx = first_new;
                 else if (r + 1 < R) nx = su[(r + 1) * kThreads + t];
                 else nx = ld2<S>(u + o + HW);  // next shot's first plane, still old
-                un.x = rnd<S>((rho * w.x + gam * (prev.x + nx.x)) / den);
-                un.y = rnd<S>((rho * w.y + gam * (prev.y + nx.y)) / den);
+                un.x = keep<S>((rho * w.x + gam * (prev.x + nx.x)) / den, o, kKeyU);
+                un.y = keep<S>((rho * w.y + gam * (prev.y + nx.y)) / den, o + 1, kKeyU);
                 prev = un;
                 if (n == 0) first_new = un;
             } else {
-                un = make_float2(rho * w.x / den, rho * w.y / den);
+                un = make_float2(keep<S>(rho * w.x / den, o, kKeyU),
+                                 keep<S>(rho * w.y / den, o + 1, kKeyU));
             }
             if (v_out) {  // v = (u - d) + phi e, with d before this iteration's store
                 const float2 dd = ld2<S>(d + o);
@@ -281,7 +282,7 @@ tikhonov_iter_v2_kernel(S *__restrict__ u, S *__restrict__ d, const float *__res
                                                                      by ? gy + ey : gy);
             }
             st2<S>(u + o, un);
-            st2<S>(d + o, make_float2(w.x - un.x, w.y - un.y));
+            st2<S>(d + o, make_float2(keep<S>(w.x - un.x, o, kKeyD), keep<S>(w.y - un.y, o + 1, kKeyD)));
         }
     }
 }

@@ -322,12 +322,16 @@ __global__ void __launch_bounds__(B * 32) tvz_sweep_kernel(const ZsArgs a)
                     const float ux = g[i].x - a.theta * dx;
                     const float uy = g[i].y - a.theta * dy;
                     if (ownr[i] && ownc[0]) {
-                        st<S>(un + (size_t)off[i], ux);
-                        if (dn) st<S>(dn + (size_t)off[i], wo[i].x - rnd<S>(ux));
+                        const size_t vi = (size_t)n * HW + (size_t)off[i];
+                        const float ur = keep<S>(ux, vi, kKeyU);
+                        st<S>(un + (size_t)off[i], ur);
+                        if (dn) st<S>(dn + (size_t)off[i], keep<S>(wo[i].x - ur, vi, kKeyD));
                     }
                     if (ownr[i] && ownc[1]) {
-                        st<S>(un + (size_t)off[i] + 1, uy);
-                        if (dn) st<S>(dn + (size_t)off[i] + 1, wo[i].y - rnd<S>(uy));
+                        const size_t vi = (size_t)n * HW + (size_t)off[i] + 1;
+                        const float ur = keep<S>(uy, vi, kKeyU);
+                        st<S>(un + (size_t)off[i] + 1, ur);
+                        if (dn) st<S>(dn + (size_t)off[i] + 1, keep<S>(wo[i].y - ur, vi, kKeyD));
                     }
                 }
             }

@@ -185,4 +185,45 @@ __device__ __forceinline__ float rnd(float v)
     return ld<S>(&t);
 }
 
+// The value a state store keeps.  FP32: v.  FP16: v rounded to nearest even.
+// BF16: v rounded stochastically: the part of v below the BF16 ulp decides the
+// direction with a threshold drawn from a hash of v's own bits, the voxel index
+// and the field (u, d or w).  Round-to-nearest in BF16 loses the small late
+// updates of a converging ADMM iteration (they fall below half an ulp and are
+// rounded away, so the iterates stall early); stochastic rounding keeps them on
+// average.  The threshold depends only on (value, index, field), so the same
+// value at the same voxel is rounded the same way in every kernel and run.
+constexpr unsigned kKeyU = 0x68e31da4u, kKeyD = 0xb5297a4du, kKeyW = 0x1b56c4e9u;
+
+// 16-bit rounding threshold from (value bits, index, field): a multiply-add
+// of the three and one multiply-xorshift round, the high bits taken.
+__device__ __forceinline__ unsigned sr_threshold(unsigned b, size_t idx, unsigned field)
+{
+    unsigned h = (b ^ field) * 0x9e3779b1u + (unsigned)idx * 0x85ebca77u;
+    h ^= h >> 15;
+    h *= 0x2c1b3c6du;
+    h ^= h >> 12;
+    return h >> 16;
+}
+
+template <typename S>
+__device__ __forceinline__ float keep(float v, size_t idx, unsigned field);
+template <>
+__device__ __forceinline__ float keep<float>(float v, size_t, unsigned)
+{
+    return v;
+}
+template <>
+__device__ __forceinline__ float keep<__half>(float v, size_t, unsigned)
+{
+    return rnd<__half>(v);
+}
+template <>
+__device__ __forceinline__ float keep<__nv_bfloat16>(float v, size_t idx, unsigned field)
+{
+    const unsigned b = __float_as_uint(v);
+    if ((b & 0x7f800000u) == 0x7f800000u) return rnd<__nv_bfloat16>(v);  // inf, nan
+    return __uint_as_float((b + sr_threshold(b, idx, field)) & 0xffff0000u);
+}
+
 }  // namespace cslsm

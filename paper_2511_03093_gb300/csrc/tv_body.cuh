@@ -334,8 +334,10 @@ __device__ __forceinline__ void tv_tile_body(const TvLaunch &a, int bx, int by, 
         if (a.write_final) {
             const float divp = (A1[l] - A1[l - PW]) + (A2[l] - A2[l - 1]);
             const float uv = sg[l] - a.theta * divp;
-            st<S>((S *)a.u + (size_t)n * HW + o, uv);
-            if (a.d) st<S>((S *)a.d + (size_t)n * HW + o, ld_l2<S>(wn + o) - rnd<S>(uv));
+            const size_t vi = (size_t)n * HW + o;
+            const float ur = keep<S>(uv, vi, kKeyU);
+            st<S>((S *)a.u + vi, ur);
+            if (a.d) st<S>((S *)a.d + vi, keep<S>(ld_l2<S>(wn + o) - ur, vi, kKeyD));
         } else {
             a.pout[(size_t)sl * HW + o] = A1[l];
             a.pout[(size_t)(a.nslices + sl) * HW + o] = A2[l];
