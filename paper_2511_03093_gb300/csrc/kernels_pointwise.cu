@@ -161,7 +161,9 @@ tikhonov_iter_kernel(S *__restrict__ u, S *__restrict__ d, const float *__restri
     if (stop && *stop) return;
     const int p = blockIdx.x * kThreads + threadIdx.x;
     const int Z = N * R;
-    const float den = 2.f * lam + rho + 2.f * gam;
+    // one reciprocal per thread: the per-voxel divisions cost more issue slots
+    // than the kernel's memory traffic leaves (the u-update multiplies by it)
+    const float inv_den = 1.f / (2.f * lam + rho + 2.f * gam);
     double sdv = 0.0, sv = 0.0;
     if (p < HW) {
         float prev = gam > 0.f ? ld<S>(u + (Z - 1) * HW + p) : 0.f;  // u_{Z-1}, not yet updated
@@ -194,11 +196,11 @@ tikhonov_iter_kernel(S *__restrict__ u, S *__restrict__ d, const float *__restri
                         if (n == Z - 1) next = first_new;
                         else if (r + 1 < R) next = ur[r + 1 < RMAX ? r + 1 : r];
                         else next = ld<S>(u + o + HW);  // next shot's first plane, still old
-                        un = keep<S>((rho * w + gam * (prev + next)) / den, (size_t)o, kKeyU);
+                        un = keep<S>((rho * w + gam * (prev + next)) * inv_den, (size_t)o, kKeyU);
                         prev = un;
                         if (n == 0) first_new = un;
                     } else {
-                        un = keep<S>(rho * w / den, (size_t)o, kKeyU);
+                        un = keep<S>(rho * w * inv_den, (size_t)o, kKeyU);
                     }
                     st<S>(u + o, un);
                     st<S>(d + o, keep<S>(w - un, (size_t)o, kKeyD));
@@ -236,7 +238,9 @@ tikhonov_iter_v2_kernel(S *__restrict__ u, S *__restrict__ d, const float *__res
     const int p = 2 * (blockIdx.x * kThreads + t);
     if (p >= HW) return;
     const int Z = N * R;
-    const float den = 2.f * lam + rho + 2.f * gam;
+    // one reciprocal per thread: the per-voxel divisions cost more issue slots
+    // than the kernel's memory traffic leaves (the u-update multiplies by it)
+    const float inv_den = 1.f / (2.f * lam + rho + 2.f * gam);
     float2 prev = gam > 0.f ? ld2<S>(u + (size_t)(Z - 1) * HW + p) : make_float2(0.f, 0.f);
     float2 first_new = make_float2(0.f, 0.f);
     for (int j = 0; j < N; ++j) {
@@ -267,13 +271,13 @@ tikhonov_iter_v2_kernel(S *__restrict__ u, S *__restrict__ d, const float *__res
                 if (n == Z - 1) nx = first_new;
                 else if (r + 1 < R) nx = su[(r + 1) * kThreads + t];
                 else nx = ld2<S>(u + o + HW);  // next shot's first plane, still old
-                un.x = keep<S>((rho * w.x + gam * (prev.x + nx.x)) / den, o, kKeyU);
-                un.y = keep<S>((rho * w.y + gam * (prev.y + nx.y)) / den, o + 1, kKeyU);
+                un.x = keep<S>((rho * w.x + gam * (prev.x + nx.x)) * inv_den, o, kKeyU);
+                un.y = keep<S>((rho * w.y + gam * (prev.y + nx.y)) * inv_den, o + 1, kKeyU);
                 prev = un;
                 if (n == 0) first_new = un;
             } else {
-                un = make_float2(keep<S>(rho * w.x / den, o, kKeyU),
-                                 keep<S>(rho * w.y / den, o + 1, kKeyU));
+                un = make_float2(keep<S>(rho * w.x * inv_den, o, kKeyU),
+                                 keep<S>(rho * w.y * inv_den, o + 1, kKeyU));
             }
             if (v_out) {  // v = (u - d) + phi e, with d before this iteration's store
                 const float2 dd = ld2<S>(d + o);
