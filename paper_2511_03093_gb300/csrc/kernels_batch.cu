@@ -67,6 +67,7 @@ struct BItem {
     int H, W, N, R, Z;
     int hh, hc, TH, TW, tiles_x, tiles;  // row / column halo, tile rows / columns
     int units_x;
+    int xpair;            // x-update: two adjacent pixels per thread (H W even)
     long long units_lvl;  // TV units per level
     long long units_iter;
 };
@@ -146,6 +147,44 @@ __device__ void xupdate_unit(const BItem &it, int unit, float rho, bool last)
             const float v = ((word >> r) & 1u) ? g + e : g;
             st<S>(w + o, keep<S>(v + dr, o, kKeyW));
             if (last) it.v_out[o] = v;
+        }
+    }
+}
+
+// The same x-update, two adjacent pixels per thread (H W even: the pairs are
+// aligned), one access per field and plane for both; per pixel the same
+// operations in the same order.
+template <typename S>
+__device__ void xupdate_unit2(const BItem &it, int unit, float rho, bool last)
+{
+    const int HW = it.H * it.W;
+    const int pix = 2 * (unit * kBNT + threadIdx.x);
+    if (pix >= HW) return;
+    const S *u = (const S *)it.u, *d = (const S *)it.d;
+    S *w = (S *)it.w;
+    for (int j = 0; j < it.N; ++j) {
+        const uint2 word = __ldcg(reinterpret_cast<const uint2 *>(it.words + (size_t)j * it.wstride + pix));
+        const size_t base = (size_t)j * it.R * HW + pix;
+        float sx = 0.f, sy = 0.f;
+#pragma unroll 8
+        for (int r = 0; r < it.R; ++r) {
+            const size_t o = base + (size_t)r * HW;
+            const float2 uu = ld2_l2<S>(u + o), dd = ld2_l2<S>(d + o);
+            if ((word.x >> r) & 1u) sx += uu.x - dd.x;
+            if ((word.y >> r) & 1u) sy += uu.y - dd.y;
+        }
+        const float2 bb = __ldcg(reinterpret_cast<const float2 *>(it.b + (size_t)j * HW + pix));
+        const float ex = (bb.x - sx) / (rho + (float)__popc(word.x));
+        const float ey = (bb.y - sy) / (rho + (float)__popc(word.y));
+#pragma unroll 8
+        for (int r = 0; r < it.R; ++r) {
+            const size_t o = base + (size_t)r * HW;
+            const float2 dd = ld2_l2<S>(d + o), uu = ld2_l2<S>(u + o);
+            const float gx = uu.x - dd.x, gy = uu.y - dd.y;
+            const float vx = ((word.x >> r) & 1u) ? gx + ex : gx;
+            const float vy = ((word.y >> r) & 1u) ? gy + ey : gy;
+            st2<S>(w + o, make_float2(keep<S>(vx + dd.x, o, kKeyW), keep<S>(vy + dd.y, o + 1, kKeyW)));
+            if (last) *reinterpret_cast<float2 *>(it.v_out + o) = make_float2(vx, vy);
         }
     }
 }
@@ -394,7 +433,8 @@ __global__ void __launch_bounds__(kBNT, 2) batch_persistent_kernel(const BDesc *
         __syncthreads();
         if (s_abort) break;
         if (p == 0) {
-            xupdate_unit<S>(it, unit, D.rho, k == D.iters - 1);
+            if (it.xpair) xupdate_unit2<S>(it, unit, D.rho, k == D.iters - 1);
+            else xupdate_unit<S>(it, unit, D.rho, k == D.iters - 1);
         } else {
             // level p: slice n, phase j (gamma > 0), or phase j of every slice
             const int q = p - 1;
@@ -473,7 +513,10 @@ cslsm_status batch_build(const BatchSpec &spec, BatchRun &run)
         b.TW = kBPW - 2 * b.hc;
         b.tiles_x = (s.W + b.TW - 1) / b.TW;
         b.tiles = b.tiles_x * ((s.H + b.TH - 1) / b.TH);
-        b.units_x = (s.H * s.W + kBNT - 1) / kBNT;
+        // pairs need H W even and the caller's b and v_out 8-byte aligned (the
+        // plan's buffers are)
+        b.xpair = (s.H * s.W) % 2 == 0 && ((uintptr_t)s.b | (uintptr_t)s.v_out) % 8 == 0;
+        b.units_x = b.xpair ? (s.H * s.W / 2 + kBNT - 1) / kBNT : (s.H * s.W + kBNT - 1) / kBNT;
         const bool chain = zs && b.Z > 1;  // Gauss-Seidel: one level per slice and phase
         b.units_lvl = chain ? b.tiles : (long long)b.tiles * b.Z;
         const int lv = chain ? b.Z * P : P;
