@@ -47,7 +47,7 @@ L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 DOMINANT = "batch_persistent"  # one launch = the whole 60-iteration batch
 DOMINANT_SOURCES = ("kernels_batch.cu", "tv_body.cuh", "storage.cuh")
 TVZ_DOMINANT = "tvz_sweep"  # the single-volume configuration's dominant kernel
-TVZ_SOURCES = ("kernels_tvz.cu", "tv_body.cuh")
+TVZ_SOURCES = ("kernels_tvz.cu", "tv_body.cuh", "storage.cuh")
 TIMING_PERIOD = 1  # every launch of each kernel timed with CUDA events
 ORACLE_SAMPLE_ITERS = 2  # bounded CPU sample: ADMM iterations per sampled item
 
@@ -737,6 +737,21 @@ def run_secondary(args) -> None:
     if name == "tvz_512x512x16":
         run_tvz(args)
         return
+    known = ("batched_8x6", "tikhonov_1024x1024x32", "tikhonovz_1024x1024x32", "tv_1024x1024x32",
+             "bm3d_1024x1024x32", "tv_128x128x8", "unrolled_b8", "unrolled_b1",
+             "wnnm_512x512x16", "tol_caps_512x512x16", "cr_sweep_256x256x40")
+    if name not in known:
+        raise SystemExit(f"unknown workload {name}")
+    # clocks and throttle reasons over the whole workload (the warm-up included)
+    gpu_id = None
+    try:
+        gpu_id = str(torch.cuda.get_device_properties(dev).uuid)
+        if gpu_id and not gpu_id.startswith("GPU-"):
+            gpu_id = "GPU-" + gpu_id
+    except Exception:
+        gpu_id = None
+    clocks = ClockSampler(gpu_id)
+    t_start = time.time()
     if name in ("tikhonov_1024x1024x32", "tikhonovz_1024x1024x32", "tv_1024x1024x32",
                 "bm3d_1024x1024x32", "tv_128x128x8"):
         wk = synth.WORKLOADS["tv_128x128x8" if name == "tv_128x128x8" else "bm3d_1024x1024x32"]
@@ -916,6 +931,8 @@ def run_secondary(args) -> None:
                    volume=[Z, H, W], sweep=rows)
     else:
         raise SystemExit(f"unknown workload {name}")
+    clocks.window(t_start, time.time())
+    out["clocks"] = clocks.stop()
     print(json.dumps(out), flush=True)
 
 
