@@ -113,17 +113,36 @@ def _kernel_hash(sources=DOMINANT_SOURCES) -> str:
     return h.hexdigest()[:16]
 
 
-def _traffic(kernel: str, workload: str, sources) -> float | None:
-    """DRAM bytes per launch of a kernel from its committed ncu record, if that
-    record was taken on the kernel's sources as they are now."""
+def _record(kernel: str, workload: str, sources) -> dict:
+    """A kernel's committed ncu record, if it was taken on the kernel's sources
+    as they are now; else an empty record."""
     p = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.json")
     try:
         rec = json.load(open(p))
     except (OSError, ValueError):
-        return None
+        return {}
     if rec.get("sources_sha256_16") != _kernel_hash(sources):
+        return {}
+    return rec
+
+
+def _traffic(kernel: str, workload: str, sources) -> float | None:
+    """DRAM bytes per launch of a kernel from its committed ncu record."""
+    return _record(kernel, workload, sources).get("dram_bytes_per_launch")
+
+
+def _l2(kernel: str, workload: str, sources, avg_launch_s: float) -> dict | None:
+    """L2 throughput of a kernel whose working set is L2-resident: the L2 bytes
+    per launch of its ncu record over the launch time measured in this run,
+    against the L2 sector peak of the same record."""
+    rec = _record(kernel, workload, sources)
+    if "l2_bytes_per_launch" not in rec or avg_launch_s <= 0:
         return None
-    return rec.get("dram_bytes_per_launch")
+    gbs = rec["l2_bytes_per_launch"] / avg_launch_s / 1e9
+    return {"bytes_per_launch": rec["l2_bytes_per_launch"], "achieved": gbs, "unit": "GB/s",
+            "peak": rec["l2_peak_GBs"], "frac": gbs / rec["l2_peak_GBs"],
+            "hit_rate_pct": rec.get("l2_sector_hit_rate_pct"),
+            "source": "L2 bytes from ncu (lts__t_sectors x 32 B), launch time from this run"}
 
 
 def _quality(cs, v, data, dev):
@@ -655,6 +674,8 @@ def run_tvz(args) -> None:
                     "avg_launch_us": avg_s * 1e6, "launches_timed": n_dom,
                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
                     "share_of_step": ms_dom * 4 / total_ms}
+            # the working set (16.8 MB per field) is L2-resident: report L2 throughput
+            roof["l2"] = _l2(TVZ_DOMINANT, "tvz_512x512x16", TVZ_SOURCES, avg_s)
         cpu = cpu_baseline_tvz(data, PARAMS_TVZ["iters"]) if world == 1 or rank == 0 else None
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
