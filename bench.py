@@ -518,6 +518,7 @@ def run_ours(args) -> None:
         b32_ms = e0.elapsed_time(e1)
         batch32.wait()
         ps_b32 = [float(cs.psnr(v, x)) for v, x in zip(v_p, x_d)]
+        sched32 = batch32.info()
         batch32.close()
         cpu = cpu_baseline(ws, datas) if world == 1 else None
         out = {
@@ -540,7 +541,9 @@ def run_ours(args) -> None:
                          "max_dpsnr_bf16_vs_plain_fp32_db": max(abs(a - b) for a, b in
                                                                 zip(ps_batch, ps_plain)),
                          "max_dpsnr_fp32_batched_vs_plain_db": max(abs(a - b) for a, b in
-                                                                   zip(ps_b32, ps_plain))},
+                                                                   zip(ps_b32, ps_plain)),
+                         "batched_fp32_schedule": sched32},
+            "schedule": batch.info(),
             "quality": {"psnr_db_mean": float(np.mean(ps_batch)),
                         "psnr_db_min": float(np.min(ps_batch))},
         }

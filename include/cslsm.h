@@ -235,6 +235,12 @@ typedef struct {
 cslsm_status cslsm_batch_create(cslsm_batch *batch, const cslsm_batch_item *items, int n_items,
                                 const cslsm_admm_params *params, void *stream);
 
+/* The batch's schedule: Chambolle steps per phase (chosen by cslsm_set_autotune(1)
+ * timing, else the default), CTAs of the persistent launch, and work units per
+ * ADMM iteration.  Any output pointer may be NULL.  Host-only; no stream work. */
+cslsm_status cslsm_batch_info(cslsm_batch batch, int *steps_per_phase, int *grid,
+                              long long *units_per_iteration);
+
 /* Enqueue one whole batched solve on `stream` (one graph launch). */
 cslsm_status cslsm_batch_run(cslsm_batch batch, void *stream);
 

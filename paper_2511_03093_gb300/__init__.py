@@ -133,6 +133,9 @@ def lib() -> ctypes.CDLL:
     for name in ("cslsm_batch_run", "cslsm_batch_wait"):
         getattr(L, name).argtypes = [P, P]
         getattr(L, name).restype = I
+    L.cslsm_batch_info.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I),
+                                   ctypes.POINTER(ctypes.c_longlong)]
+    L.cslsm_batch_info.restype = I
     L.cslsm_batch_set_wait_limit.argtypes = [P, ctypes.c_double, I]
     L.cslsm_batch_set_wait_limit.restype = I
     L.cslsm_batch_destroy.argtypes = [P]
@@ -459,6 +462,14 @@ class Batch:
 
     def wait(self, stream=None) -> None:
         _check(lib().cslsm_batch_wait(self._h, _stream(stream)), "cslsm_batch_wait")
+
+    def info(self) -> dict:
+        """The schedule: Chambolle steps per phase, CTAs of the persistent
+        launch, work units per ADMM iteration."""
+        k, grid, units = ctypes.c_int(), ctypes.c_int(), ctypes.c_longlong()
+        _check(lib().cslsm_batch_info(self._h, ctypes.byref(k), ctypes.byref(grid),
+                                      ctypes.byref(units)), "cslsm_batch_info")
+        return {"steps_per_phase": k.value, "grid": grid.value, "units_per_iteration": units.value}
 
     def set_wait_limit(self, seconds: float, test_stall: bool = False) -> None:
         _check(lib().cslsm_batch_set_wait_limit(self._h, float(seconds), int(test_stall)),

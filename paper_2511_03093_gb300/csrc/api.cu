@@ -638,12 +638,18 @@ cslsm_status cslsm_batch_create(cslsm_batch *out, const cslsm_batch_item *items,
                 cudaEvent_t e0, e1;
                 cudaEventCreate(&e0);
                 cudaEventCreate(&e1);
-                for (auto &z : probe.zero) cudaMemsetAsync(z.first, 0, z.second, s);
-                cudaEventRecord(e0, s);
-                st = batch_enqueue(probe.run, s);
-                cudaEventRecord(e1, s);
-                if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1))
-                    ms = 1e30f;
+                // two runs, the faster one counts: the first launch of a
+                // candidate may carry one-time costs
+                for (int rep = 0; rep < 2 && !st; ++rep) {
+                    for (auto &z : probe.zero) cudaMemsetAsync(z.first, 0, z.second, s);
+                    cudaEventRecord(e0, s);
+                    st = batch_enqueue(probe.run, s);
+                    cudaEventRecord(e1, s);
+                    float t = 1e30f;
+                    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1))
+                        t = 1e30f;
+                    ms = std::min(ms, t);
+                }
                 cudaEventDestroy(e0);
                 cudaEventDestroy(e1);
             }
@@ -666,6 +672,16 @@ cslsm_status cslsm_batch_create(cslsm_batch *out, const cslsm_batch_item *items,
         return st;
     }
     *out = bt;
+    return CSLSM_OK;
+}
+
+cslsm_status cslsm_batch_info(cslsm_batch batch, int *steps_per_phase, int *grid,
+                              long long *units_per_iteration)
+{
+    CHECK_ARG(batch != nullptr, "batch is NULL");
+    if (steps_per_phase) *steps_per_phase = batch->run.k;
+    if (grid) *grid = batch->run.grid;
+    if (units_per_iteration) *units_per_iteration = batch->run.units_iter;
     return CSLSM_OK;
 }
 

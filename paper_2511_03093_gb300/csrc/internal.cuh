@@ -227,6 +227,8 @@ struct BatchRun {
     int *error = nullptr;
     size_t smem = 0;
     int grid = 0, storage = 0;
+    int k = 0;                  // Chambolle steps per phase
+    long long units_iter = 0;   // work units per iteration
 };
 
 // ---- differentiable unrolled solver (kernels_diff.cu) -------------------------

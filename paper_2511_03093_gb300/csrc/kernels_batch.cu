@@ -3,7 +3,8 @@
 // persistent kernel launch, captured once in a CUDA graph and replayed.
 //
 // Work decomposition.  For every item (measurement) an iteration is a chain of
-// phases: the x-update (Eq. v-update, units of 256 pixel columns), then the
+// phases: the x-update (Eq. v-update, units of 256 threads of 1, 2 or 4 adjacent
+// pixel columns, as the alignment of H W and the caller's buffers allows), then the
 // TV u-step cut into phases of at most k Chambolle steps.  A TV unit is one
 // tile of one slice for one phase: it forms g on its region (the tile plus a
 // halo of k + 1 pixels; with gamma > 0 from the newest u_{n-1} and the previous
@@ -52,9 +53,11 @@
 namespace cslsm {
 namespace {
 
-constexpr int kBW = 8, kBR = 8;      // warps per CTA, rows of the region per warp
+constexpr int kBW = 8, kBR = 12;     // warps per CTA, rows of the region per warp
 constexpr int kBNT = kBW * 32;       // 256 threads per CTA, two CTAs per SM
 constexpr int kBRH = kBW * kBR + 2;  // region rows
+// a warp's row masks hold 2 bits (columns) for each of its kBR + 1 rows
+static_assert(2 * (kBR + 1) <= 32, "row masks are 32-bit");
 constexpr int kBPW = 64;             // region columns
 
 struct BItem {
@@ -67,7 +70,7 @@ struct BItem {
     int H, W, N, R, Z;
     int hh, hc, TH, TW, tiles_x, tiles;  // row / column halo, tile rows / columns
     int units_x;
-    int xpair;            // x-update: two adjacent pixels per thread (H W even)
+    int xvec;             // x-update pixels per thread: 1, 2 (H W even), 4 (H W % 4 == 0)
     long long units_lvl;  // TV units per level
     long long units_iter;
 };
@@ -189,11 +192,57 @@ __device__ void xupdate_unit2(const BItem &it, int unit, float rho, bool last)
     }
 }
 
+// The same x-update, four adjacent pixels per thread (H W a multiple of 4: the
+// quads are aligned), one access per field and plane for all four; per pixel
+// the same operations in the same order.
+template <typename S>
+__device__ void xupdate_unit4(const BItem &it, int unit, float rho, bool last)
+{
+    const int HW = it.H * it.W;
+    const int pix = 4 * (unit * kBNT + threadIdx.x);
+    if (pix >= HW) return;
+    const S *u = (const S *)it.u, *d = (const S *)it.d;
+    S *w = (S *)it.w;
+    for (int j = 0; j < it.N; ++j) {
+        const uint4 word = __ldcg(reinterpret_cast<const uint4 *>(it.words + (size_t)j * it.wstride + pix));
+        const size_t base = (size_t)j * it.R * HW + pix;
+        float4 sm = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 8
+        for (int r = 0; r < it.R; ++r) {
+            const size_t o = base + (size_t)r * HW;
+            const float4 uu = ld4_l2<S>(u + o), dd = ld4_l2<S>(d + o);
+            if ((word.x >> r) & 1u) sm.x += uu.x - dd.x;
+            if ((word.y >> r) & 1u) sm.y += uu.y - dd.y;
+            if ((word.z >> r) & 1u) sm.z += uu.z - dd.z;
+            if ((word.w >> r) & 1u) sm.w += uu.w - dd.w;
+        }
+        const float4 bb = __ldcg(reinterpret_cast<const float4 *>(it.b + (size_t)j * HW + pix));
+        const float ex = (bb.x - sm.x) / (rho + (float)__popc(word.x));
+        const float ey = (bb.y - sm.y) / (rho + (float)__popc(word.y));
+        const float ez = (bb.z - sm.z) / (rho + (float)__popc(word.z));
+        const float ew = (bb.w - sm.w) / (rho + (float)__popc(word.w));
+#pragma unroll 4
+        for (int r = 0; r < it.R; ++r) {
+            const size_t o = base + (size_t)r * HW;
+            const float4 dd = ld4_l2<S>(d + o), uu = ld4_l2<S>(u + o);
+            const float gx = uu.x - dd.x, gy = uu.y - dd.y, gz = uu.z - dd.z, gw = uu.w - dd.w;
+            const float vx = ((word.x >> r) & 1u) ? gx + ex : gx;
+            const float vy = ((word.y >> r) & 1u) ? gy + ey : gy;
+            const float vz = ((word.z >> r) & 1u) ? gz + ez : gz;
+            const float vw = ((word.w >> r) & 1u) ? gw + ew : gw;
+            st4<S>(w + o, make_float4(keep<S>(vx + dd.x, o, kKeyW), keep<S>(vy + dd.y, o + 1, kKeyW),
+                                      keep<S>(vz + dd.z, o + 2, kKeyW), keep<S>(vw + dd.w, o + 3, kKeyW)));
+            if (last) *reinterpret_cast<float4 *>(it.v_out + o) = make_float4(vx, vy, vz, vw);
+        }
+    }
+}
+
 // Phase j (of D.P) of slice n's TV prox on tile `tile` of item it: g on the
 // region, p from the previous phase (or 0), ns Chambolle steps with the rows
 // in registers, then p of the own tile (or the final u, d) back to memory.
 template <typename S>
-__device__ void tv_unit(const BItem &it, const BDesc &D, int n, int j, int tile, Bnd<kBW> &sb)
+__device__ void tv_unit(const BItem &it, const BDesc &D, int n, int j, int tile, Bnd<kBW> &sb,
+                        float2 *s_g)
 {
     constexpr unsigned FULL = 0xffffffffu;
     constexpr int B = kBW, RPW = kBR, NR = kBR + 1, RH = kBRH;
@@ -270,6 +319,13 @@ __device__ void tv_unit(const BItem &it, const BDesc &D, int n, int j, int tile,
         for (int i = 0; i < RPW; ++i) g[i] = make_float2(gv[2 * i], gv[2 * i + 1]);
         gdn = make_float2(gv[2 * RPW], gv[2 * RPW + 1]);
     }
+    // g of the warp's rows stays in shared memory over the steps (registers go
+    // to the dual field); each warp reads only its own rows
+    float2 *sgw = s_g + wp * RPW * 32;
+    {
+#pragma unroll
+        for (int i = 0; i < RPW; ++i) sgw[i * 32 + lane] = g[i];
+    }
     const int Zp = gam > 0.f ? 1 : it.Z, slot = gam > 0.f ? 0 : n;
     float2 p1[RPW], p2[RPW];
     float2 f1 = make_float2(0.f, 0.f), f2 = make_float2(0.f, 0.f);
@@ -334,24 +390,40 @@ __device__ void tv_unit(const BItem &it, const BDesc &D, int n, int j, int tile,
     const int ns = min(D.k, D.T - j * D.k);
     // rows exact after the phase: the own tile, and the row above it for u_n
     const int lo = hh - (j == D.P - 1 ? 1 : 0), hi = hh + TH;
+    const float2 *sgr = sgw;
     if (interior)
-        sweep_steps<true, B, RPW>(sb, p1, p2, g, gdn, mr, mc0, mc1, inv_theta, D.tau, ns, wp,
+        sweep_steps<true, B, RPW>(sb, p1, p2, sgr, gdn, mr, mc0, mc1, inv_theta, D.tau, ns, wp,
                                   lane, lo, hi);
     else
-        sweep_steps<false, B, RPW>(sb, p1, p2, g, gdn, mr, mc0, mc1, inv_theta, D.tau, ns, wp,
+        sweep_steps<false, B, RPW>(sb, p1, p2, sgr, gdn, mr, mc0, mc1, inv_theta, D.tau, ns, wp,
                                    lane, lo, hi);
+    // Every row pairs up (pairm full) only when W is even, so every plane and
+    // buffer offset is even and a lane's two columns take one aligned access.
+    // The column halo and the tile width are even, so the two columns are then
+    // owned together: bit 2i of ownm stands for both.
+    const bool pairs = pairm == (1u << NR) - 1;
     if (j < D.P - 1) {  // p of the own tile for the next phase
         float *Q1 = it.pbuf + ((size_t)(j & 1) * 2 * Zp + slot) * HW;
         float *Q2 = Q1 + (size_t)Zp * HW;
+        if (pairs) {
 #pragma unroll
-        for (int i = 0; i < RPW; ++i) {
-            if (ownm & (1u << (2 * i))) {
-                Q1[off[i]] = p1[i].x;
-                Q2[off[i]] = p2[i].x;
+            for (int i = 0; i < RPW; ++i) {
+                if (ownm & (1u << (2 * i))) {
+                    *reinterpret_cast<float2 *>(Q1 + off[i]) = p1[i];
+                    *reinterpret_cast<float2 *>(Q2 + off[i]) = p2[i];
+                }
             }
-            if (ownm & (1u << (2 * i + 1))) {
-                Q1[off[i] + 1] = p1[i].y;
-                Q2[off[i] + 1] = p2[i].y;
+        } else {
+#pragma unroll
+            for (int i = 0; i < RPW; ++i) {
+                if (ownm & (1u << (2 * i))) {
+                    Q1[off[i]] = p1[i].x;
+                    Q2[off[i]] = p2[i].x;
+                }
+                if (ownm & (1u << (2 * i + 1))) {
+                    Q1[off[i] + 1] = p1[i].y;
+                    Q2[off[i] + 1] = p2[i].y;
+                }
             }
         }
     } else {  // u_n = g - theta div p^T and d_n = w_n - u_n on the own tile
@@ -371,7 +443,8 @@ __device__ void tv_unit(const BItem &it, const BDesc &D, int n, int j, int tile,
             const float2 pu = i == 0 ? pu0 : p1[i - 1];
             const float dx = (p1[i].x - pu.x) + (p2[i].x - p2l);
             const float dy = (p1[i].y - pu.y) + (p2[i].y - p2[i].x);
-            const float uu[2] = {g[i].x - theta * dx, g[i].y - theta * dy};
+            const float2 gi = sgw[i * 32 + lane];
+            const float uu[2] = {gi.x - theta * dx, gi.y - theta * dy};
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
                 if (!(ownm & (1u << (2 * i + c)))) continue;
@@ -389,6 +462,7 @@ template <typename S>
 __global__ void __launch_bounds__(kBNT, 2) batch_persistent_kernel(const BDesc *__restrict__ dp)
 {
     __shared__ Bnd<kBW> sb;
+    __shared__ float2 s_g[kBW * kBR * 32];  // g of each warp's rows during a TV unit
     __shared__ long long s_t;
     __shared__ int s_abort;
     const BDesc D = *dp;
@@ -433,7 +507,8 @@ __global__ void __launch_bounds__(kBNT, 2) batch_persistent_kernel(const BDesc *
         __syncthreads();
         if (s_abort) break;
         if (p == 0) {
-            if (it.xpair) xupdate_unit2<S>(it, unit, D.rho, k == D.iters - 1);
+            if (it.xvec == 4) xupdate_unit4<S>(it, unit, D.rho, k == D.iters - 1);
+            else if (it.xvec == 2) xupdate_unit2<S>(it, unit, D.rho, k == D.iters - 1);
             else xupdate_unit<S>(it, unit, D.rho, k == D.iters - 1);
         } else {
             // level p: slice n, phase j (gamma > 0), or phase j of every slice
@@ -448,7 +523,7 @@ __global__ void __launch_bounds__(kBNT, 2) batch_persistent_kernel(const BDesc *
                 n = unit / it.tiles;
                 tile = unit - n * it.tiles;
             }
-            tv_unit<S>(it, D, n, j, tile, sb);
+            tv_unit<S>(it, D, n, j, tile, sb, s_g);
         }
         // the barrier orders every thread's stores before thread 0's release
         // add; a unit that acquires the count sees them
@@ -515,8 +590,12 @@ cslsm_status batch_build(const BatchSpec &spec, BatchRun &run)
         b.tiles = b.tiles_x * ((s.H + b.TH - 1) / b.TH);
         // pairs need H W even and the caller's b and v_out 8-byte aligned (the
         // plan's buffers are)
-        b.xpair = (s.H * s.W) % 2 == 0 && ((uintptr_t)s.b | (uintptr_t)s.v_out) % 8 == 0;
-        b.units_x = b.xpair ? (s.H * s.W / 2 + kBNT - 1) / kBNT : (s.H * s.W + kBNT - 1) / kBNT;
+        {
+            const int hw = s.H * s.W;
+            const uintptr_t bv = (uintptr_t)s.b | (uintptr_t)s.v_out;
+            b.xvec = hw % 4 == 0 && bv % 16 == 0 ? 4 : hw % 2 == 0 && bv % 8 == 0 ? 2 : 1;
+            b.units_x = (hw / b.xvec + kBNT - 1) / kBNT;
+        }
         const bool chain = zs && b.Z > 1;  // Gauss-Seidel: one level per slice and phase
         b.units_lvl = chain ? b.tiles : (long long)b.tiles * b.Z;
         const int lv = chain ? b.Z * P : P;
@@ -600,6 +679,8 @@ cslsm_status batch_build(const BatchSpec &spec, BatchRun &run)
     }
     run.grid = per_sm * sms;
     run.storage = spec.storage;
+    run.k = k;
+    run.units_iter = units_iter;
     return CSLSM_OK;
 }
 

@@ -69,6 +69,32 @@ __device__ __forceinline__ float2 ld2_l2<__half>(const __half *p)
     return __half22float2(*reinterpret_cast<const __half2 *>(&r));
 }
 
+// Four consecutive elements, L2 only (16-byte aligned for float, 8-byte for
+// 16-bit types).
+template <typename S>
+__device__ __forceinline__ float4 ld4_l2(const S *p);
+template <>
+__device__ __forceinline__ float4 ld4_l2<float>(const float *p)
+{
+    return __ldcg(reinterpret_cast<const float4 *>(p));
+}
+template <>
+__device__ __forceinline__ float4 ld4_l2<__nv_bfloat16>(const __nv_bfloat16 *p)
+{
+    const uint2 r = __ldcg(reinterpret_cast<const uint2 *>(p));
+    const float2 fa = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&r.x));
+    const float2 fb = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&r.y));
+    return make_float4(fa.x, fa.y, fb.x, fb.y);
+}
+template <>
+__device__ __forceinline__ float4 ld4_l2<__half>(const __half *p)
+{
+    const uint2 r = __ldcg(reinterpret_cast<const uint2 *>(p));
+    const float2 fa = __half22float2(*reinterpret_cast<const __half2 *>(&r.x));
+    const float2 fb = __half22float2(*reinterpret_cast<const __half2 *>(&r.y));
+    return make_float4(fa.x, fa.y, fb.x, fb.y);
+}
+
 template <typename S>
 __device__ __forceinline__ void st(S *p, float v);
 template <>

@@ -5,6 +5,8 @@
 
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "storage.cuh"
 
 namespace cslsm {
@@ -149,6 +151,18 @@ struct Bnd {
     float2 dn2[2][B][32];
 };
 
+// Row i of g for a lane: from a register array of the warp's rows, or from the
+// warp's rows in shared memory ([RPW][32] float2), which frees 2 RPW registers
+// for taller regions at one shared load per row and step.
+template <typename G>
+__device__ __forceinline__ float2 g_row(const G &g, int i, int lane)
+{
+    if constexpr (std::is_pointer<G>::value)
+        return g[i * 32 + lane];
+    else
+        return g[i];
+}
+
 // ns Chambolle steps on the warp's rows (registers) with one barrier per step.
 // INTERIOR: the CTA's whole region lies inside the image, all masks are one.
 //
@@ -160,9 +174,11 @@ struct Bnd {
 // the stale rows it leaves, in registers and in the boundary-row buffers, are
 // read only by rows outside the band of the next step, so the rows that
 // matter get exactly the values of a full update.
-template <bool INTERIOR, int B, int RPW>
+//
+// g (constant over the steps) is read through g_row.
+template <bool INTERIOR, int B, int RPW, typename G>
 __device__ __forceinline__ void sweep_steps(Bnd<B> &sb, float2 (&p1)[RPW], float2 (&p2)[RPW],
-                                            const float2 (&g)[RPW], float2 gdn,
+                                            const G &g, float2 gdn,
                                             const float (&mr)[RPW], float mc0, float mc1,
                                             float inv_theta, float tau, int ns, int wp, int lane,
                                             int lo, int hi)
@@ -179,7 +195,7 @@ __device__ __forceinline__ void sweep_steps(Bnd<B> &sb, float2 (&p1)[RPW], float
 #pragma unroll
             for (int i = 0; i < RPW; ++i)
                 q[i] = q_pair(p1[i], i == 0 ? pu0 : p1[i - 1], p2[i],
-                              __shfl_up_sync(FULL, p2[i].y, 1), g[i], inv_theta);
+                              __shfl_up_sync(FULL, p2[i].y, 1), g_row(g, i, lane), inv_theta);
             q[RPW] = q_pair(dn1, p1[RPW - 1], dn2, __shfl_up_sync(FULL, dn2.y, 1), gdn, inv_theta);
 #pragma unroll
             for (int i = 0; i < RPW; ++i) {

@@ -107,6 +107,10 @@ def test_batch_autotuned_tiles(cs):
         batch = cs.Batch(items, prm)
     finally:
         cs.set_autotune(0)
+    info = batch.info()
+    assert info["steps_per_phase"] in (7, 10, 14, 20)
+    assert info["grid"] > 0 and info["grid"] % torch.cuda.get_device_properties(0).multi_processor_count == 0
+    assert info["units_per_iteration"] > 0
     batch.run()
     batch.wait()
     for plan, b, v in items:
@@ -190,10 +194,13 @@ def test_batch_items_full_run_psnr_matches_fp64_oracle(cs, storage):
     batch.close()
 
 
-def test_batch_with_unaligned_caller_buffers(cs):
-    """Measurements and outputs that start 4 bytes past an 8-byte boundary (views
-    into larger tensors): the x-update takes its one-pixel path for them and the
-    batch still reproduces the per-volume solves bit for bit."""
+@pytest.mark.parametrize("shift", [1, 2])
+def test_batch_with_unaligned_caller_buffers(cs, shift):
+    """Measurements and outputs that start `shift` floats past a 16-byte boundary
+    (views into larger tensors): the x-update takes its one-pixel path for a
+    4-byte offset and its two-pixel path for an 8-byte one (H W is a multiple of
+    4, so aligned buffers would take the four-pixel path), and the batch still
+    reproduces the per-volume solves bit for bit."""
     import torch
 
     items = []
@@ -202,12 +209,12 @@ def test_batch_with_unaligned_caller_buffers(cs):
                            seed=1300 + k, n_blobs=20)
         data = synth.generate(w)
         plan = cs.Plan(H, W, 1, Z, to_dev(data["masks"]))
-        bbig = torch.zeros(H * W + 1, dtype=torch.float32, device="cuda")
-        bbig[1:] = to_dev(data["b"]).reshape(-1)
-        b = bbig[1:].view(1, H, W)
-        vbig = torch.empty(Z * H * W + 1, dtype=torch.float32, device="cuda")
-        v = vbig[1:].view(Z, H, W)
-        assert b.data_ptr() % 8 == 4 and v.data_ptr() % 8 == 4
+        bbig = torch.zeros(H * W + shift, dtype=torch.float32, device="cuda")
+        bbig[shift:] = to_dev(data["b"]).reshape(-1)
+        b = bbig[shift:].view(1, H, W)
+        vbig = torch.empty(Z * H * W + shift, dtype=torch.float32, device="cuda")
+        v = vbig[shift:].view(Z, H, W)
+        assert b.data_ptr() % 16 == 4 * shift and v.data_ptr() % 16 == 4 * shift
         items.append((plan, b, v))
     prm = cs.Params(rho=1.0, lam=0.05, gamma=0.2, iters=6, denoiser="tv", tv_inner=20,
                     storage="bf16")
