@@ -23,6 +23,7 @@ stratified 8-item sample of the batch (bounded iterations) on the host cores.
 from __future__ import annotations
 
 import argparse
+import atexit
 import hashlib
 import json
 import os
@@ -176,6 +177,16 @@ class ClockSampler:
             self.proc = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
+        if self.proc is not None:
+            atexit.register(self._end)  # no sampler outlives the bench, even on an error
+
+    def _end(self) -> None:
+        if self.proc is not None and self.proc.poll() is None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
 
     def window(self, t0: float, t1: float) -> None:
         """Host wall-clock bounds (time.time()) of the timed region."""
@@ -184,14 +195,26 @@ class ClockSampler:
     def stop(self):
         if self.proc is None:
             return None
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except subprocess.TimeoutExpired:
-            self.proc.kill()
+        self._end()
         self.f.close()
         return summarize_clocks(open(self.path).read().splitlines(),
                                 getattr(self, "t0", None), getattr(self, "t1", None))
+
+
+def start_clocks(dev):
+    """A clock sampler on the GPU of `dev`.  Callers start it early (before the
+    inputs are built): the first nvidia-smi start on a box can take seconds,
+    and only the samples inside the timed region are summarised."""
+    import torch
+
+    gpu_id = None
+    try:
+        gpu_id = str(torch.cuda.get_device_properties(dev).uuid)
+        if gpu_id and not gpu_id.startswith("GPU-"):
+            gpu_id = "GPU-" + gpu_id
+    except Exception:
+        gpu_id = None
+    return ClockSampler(gpu_id)
 
 
 def summarize_clocks(lines, t0=None, t1=None):
@@ -384,6 +407,7 @@ def run_ours(args) -> None:
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
     cs.lib()
+    clocks = start_clocks(dev) if rank == 0 else None
 
     n = len(ws)
     vox = sum(w.Z * w.H * w.W for w in ws)
@@ -410,14 +434,6 @@ def run_ours(args) -> None:
         if world > 1:
             dist.barrier()
 
-    gpu_id = None
-    try:
-        gpu_id = str(torch.cuda.get_device_properties(dev).uuid)
-        if gpu_id and not gpu_id.startswith("GPU-"):
-            gpu_id = "GPU-" + gpu_id
-    except Exception:
-        gpu_id = None
-    clocks = ClockSampler(gpu_id) if rank == 0 else None
     for _ in range(max(args.warmup, 0)):
         step()
     batch.wait()
@@ -577,6 +593,7 @@ def run_tvz(args) -> None:
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
     cs.lib()
+    clocks = start_clocks(dev) if rank == 0 else None
 
     w = rank_workload(rank)
     data = synth.generate(w)
@@ -601,16 +618,6 @@ def run_tvz(args) -> None:
         if world > 1:
             dist.barrier()
 
-    gpu_id = None
-    try:
-        gpu_id = str(torch.cuda.get_device_properties(dev).uuid)
-        if gpu_id and not gpu_id.startswith("GPU-"):
-            gpu_id = "GPU-" + gpu_id
-    except Exception:
-        gpu_id = None
-    # the sampler starts before the warm-up so that it is running when the timed
-    # region begins; only the samples inside the region are summarised
-    clocks = ClockSampler(gpu_id) if rank == 0 else None
     for _ in range(max(args.warmup, 0)):
         step()
     torch.cuda.synchronize()
@@ -767,14 +774,7 @@ def run_secondary(args) -> None:
     if name not in known:
         raise SystemExit(f"unknown workload {name}")
     # clocks and throttle reasons over the whole workload (the warm-up included)
-    gpu_id = None
-    try:
-        gpu_id = str(torch.cuda.get_device_properties(dev).uuid)
-        if gpu_id and not gpu_id.startswith("GPU-"):
-            gpu_id = "GPU-" + gpu_id
-    except Exception:
-        gpu_id = None
-    clocks = ClockSampler(gpu_id)
+    clocks = start_clocks(dev)
     t_start = time.time()
     if name in ("tikhonov_1024x1024x32", "tikhonovz_1024x1024x32", "tv_1024x1024x32",
                 "bm3d_1024x1024x32", "tv_128x128x8"):

@@ -623,9 +623,16 @@ cslsm_status cslsm_batch_create(cslsm_batch *out, const cslsm_batch_item *items,
     int kbest = std::min(std::max(T, 1), 10);
     if (tv_get_mode() == 1 && T > 0) {
         float best = 1e30f;
-        const int cand[] = {7, 10, 14, 20};
+        // balanced phases: ceil(T / P) steps for P = 1, 2, ... phases (a short
+        // trailing phase pays a unit's fixed loads for little work), no more
+        // than fit the region's halo, none below 5 unless T is, four at most
+        std::vector<int> cand;
+        for (int P = 1; P <= T && cand.size() < 4; ++P) {
+            const int c = (T + P - 1) / P;
+            if (c > batch_max_steps_per_phase() || c < std::min(5, T)) continue;
+            if (std::find(cand.begin(), cand.end(), c) == cand.end()) cand.push_back(c);
+        }
         for (int c : cand) {
-            if (c > T) continue;
             BatchSpec trial = spec;
             trial.iters = 1;
             trial.k = c;

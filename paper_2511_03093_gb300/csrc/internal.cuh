@@ -219,6 +219,10 @@ struct BatchSpec {
     float rho, lam, gamma, tau;
     double wait_limit_s;
 };
+// Largest number of Chambolle steps per phase whose halo fits the batched
+// solver's region.
+int batch_max_steps_per_phase();
+
 struct BatchRun {
     void *mem = nullptr;     // one device allocation (descriptors, tables, counters)
     void *desc = nullptr;

@@ -684,6 +684,16 @@ cslsm_status batch_build(const BatchSpec &spec, BatchRun &run)
     return CSLSM_OK;
 }
 
+int batch_max_steps_per_phase()
+{
+    int k = 1;
+    for (;;) {
+        const int hh = k + 2;  // the halo k + 1 steps would need
+        if (kBRH - 2 * hh < 1 || kBPW - 2 * (hh + (hh & 1)) < 2) return k;
+        ++k;
+    }
+}
+
 cslsm_status batch_set_wait(const BatchRun &run, double limit_s, int stall_test)
 {
     BDesc D{};
