@@ -46,6 +46,7 @@ METRIC = "PnP-ADMM voxel-iterations/s"
 UNIT = "voxel-it/s"
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 DOMINANT = "batch_persistent"  # one launch = the whole 60-iteration batch
+BATCH_PROFILE_K = 5  # steps per phase of the 8-item profiling case (see batched_8x6)
 DOMINANT_SOURCES = ("kernels_batch.cu", "tv_body.cuh", "storage.cuh")
 TVZ_DOMINANT = "tvz_sweep"  # the single-volume configuration's dominant kernel
 TVZ_SOURCES = ("kernels_tvz.cu", "tv_body.cuh", "storage.cuh")
@@ -836,11 +837,16 @@ def run_secondary(args) -> None:
             items.append((plan, torch.from_numpy(d["b"]).to(dev),
                           torch.empty((w.Z, w.H, w.W), dtype=torch.float32, device=dev)))
         iters = 6
+        # the phase length the 64-item batch's timing chooses (its line reports it
+        # as `schedule`): 8 items alone would time fewer, longer phases as faster
+        cs.set_batch_steps_per_phase(BATCH_PROFILE_K)
         batch = cs.Batch(items, cs.Params(**dict(PARAMS, iters=iters)))
+        cs.set_batch_steps_per_phase(0)
         ms = _timed(lambda: (batch.run(), batch.wait()), max(1, args.steps), args.warmup, flush)
         vox = sum(w.Z * w.H * w.W for w in sub)
         out.update(metric=METRIC, unit=UNIT, value=vox * iters / (sum(ms) / len(ms) / 1e3),
-                   ms_per_step=sum(ms) / len(ms), iterations=iters, items=idx, voxels=vox)
+                   ms_per_step=sum(ms) / len(ms), iterations=iters, items=idx, voxels=vox,
+                   schedule=batch.info())
         batch.close()
     elif name in ("unrolled_b8", "unrolled_b1"):
         # batch 8 with the dual iterates kept (29 GB of workspace); batch 1 with

@@ -228,12 +228,21 @@ typedef struct {
  * recorded: every run reads and writes the same buffers, and u^0 = d^0 = 0 in
  * each run.  The TV proxes run in phases of at most 10 Chambolle steps whose
  * tiles hand the dual field over through device memory the batch owns
- * (4 floats per pixel of every item, and per voxel when gamma = 0).  With
+ * (5 floats per pixel of every item with gamma > 0 and Z > 1, else 4 floats
+ * per voxel).  With
  * cslsm_set_autotune(1) the steps per phase are chosen by timing
  * one-iteration runs of a few candidates (this synchronises `stream` and
  * overwrites the items' state and v_out).  Synchronises `stream`. */
 cslsm_status cslsm_batch_create(cslsm_batch *batch, const cslsm_batch_item *items, int n_items,
                                 const cslsm_admm_params *params, void *stream);
+
+/* Chambolle steps per phase of batches created from now on (process-wide
+ * setting).  k = 0 (default): the fixed default, or the timed choice under
+ * cslsm_set_autotune(1).  k >= 1: exactly min(k, tv_inner, the largest phase
+ * whose halo fits the batch's tile region) steps, without timing (for
+ * profiling a small batch with the schedule a larger one chose).  Returns
+ * CSLSM_ERR_INVALID_ARG for k < 0. */
+cslsm_status cslsm_set_batch_steps_per_phase(int k);
 
 /* The batch's schedule: Chambolle steps per phase (chosen by cslsm_set_autotune(1)
  * timing, else the default), CTAs of the persistent launch, and work units per

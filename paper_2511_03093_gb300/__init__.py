@@ -158,6 +158,8 @@ def lib() -> ctypes.CDLL:
     L.cslsm_tv_shape.restype = I
     L.cslsm_set_autotune.argtypes = [I]
     L.cslsm_set_autotune.restype = I
+    L.cslsm_set_batch_steps_per_phase.argtypes = [I]
+    L.cslsm_set_batch_steps_per_phase.restype = I
     L.cslsm_zsweep_config.argtypes = [I, I, ctypes.c_double, I]
     L.cslsm_zsweep_config.restype = I
     L.cslsm_zsweep_num_tilings.argtypes = []
@@ -392,6 +394,12 @@ def bm3d_stage_groups(stage: int, noisy: torch.Tensor, sigma: float,
 def set_autotune(mode: int) -> None:
     """TV tile shapes: 0 cost model, 1 timed autotuning, 2..5 force a variant."""
     _check(lib().cslsm_set_autotune(int(mode)), "cslsm_set_autotune")
+
+
+def set_batch_steps_per_phase(k: int) -> None:
+    """Chambolle steps per phase of batches created from now on: 0 the default
+    (or the timed choice under set_autotune(1)), k >= 1 that many."""
+    _check(lib().cslsm_set_batch_steps_per_phase(int(k)), "cslsm_set_batch_steps_per_phase")
 
 
 def tv_shape(H: int, W: int, steps: int, nslices: int) -> dict:

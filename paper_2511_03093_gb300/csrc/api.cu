@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <atomic>
 #include <new>
 #include <utility>
 #include <vector>
@@ -514,6 +515,10 @@ cslsm_status cslsm_denoise(int denoiser, const float *in, float *out, int Z, int
 
 }  // extern "C"
 
+namespace {
+std::atomic<int> g_batch_k{0};  // cslsm_set_batch_steps_per_phase
+}  // namespace
+
 struct cslsm_batch_s {
     int device;
     BatchRun run;
@@ -618,10 +623,13 @@ cslsm_status cslsm_batch_create(cslsm_batch *out, const cslsm_batch_item *items,
         bt->zero.push_back({p->u, esz * (size_t)p->g.voxels()});
         bt->zero.push_back({p->d, esz * (size_t)p->g.voxels()});
     }
-    // steps per phase: a fixed default unless timing a few candidates on the
-    // batch itself is asked for (autotune mode 1)
+    // steps per phase: a fixed default unless a phase length is set or timing
+    // a few candidates on the batch itself is asked for (autotune mode 1)
     int kbest = std::min(std::max(T, 1), 10);
-    if (tv_get_mode() == 1 && T > 0) {
+    const int kset = g_batch_k;
+    if (kset > 0) {
+        kbest = std::min({kset, std::max(T, 1), batch_max_steps_per_phase()});
+    } else if (tv_get_mode() == 1 && T > 0) {
         float best = 1e30f;
         // balanced phases: ceil(T / P) steps for P = 1, 2, ... phases (a short
         // trailing phase pays a unit's fixed loads for little work), no more
@@ -786,6 +794,13 @@ cslsm_status cslsm_unrolled_backward(const float *logits, const float *b, int B,
     return unrolled_backward(B, Z, H, W, p->rho, p->lambda, p->gamma, p->iters, p->tv_steps,
                              p->tv_tau, p->huber_eps, p->ckpt_every, p->keep_duals, logits, b,
                              ckpt, v_bar, logits_bar, scalar_bar, ws, as_stream(stream));
+}
+
+cslsm_status cslsm_set_batch_steps_per_phase(int k)
+{
+    CHECK_ARG(k >= 0, "steps per phase must be >= 0 (0: default / timed)");
+    g_batch_k = k;
+    return CSLSM_OK;
 }
 
 cslsm_status cslsm_set_autotune(int mode)

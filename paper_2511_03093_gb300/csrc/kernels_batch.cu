@@ -8,11 +8,13 @@
 // TV u-step cut into phases of at most k Chambolle steps.  A TV unit is one
 // tile of one slice for one phase: it forms g on its region (the tile plus a
 // halo of k + 1 pixels; with gamma > 0 from the newest u_{n-1} and the previous
-// u_{n+1}, Sec. III-C), loads the dual field p that the previous phase left in
-// the item's exchange buffer (p = 0 in the first phase), runs the
-// steps with the dual field of every warp's rows in registers, and stores p of
-// its own tile for the next phase, or, in the last phase, u = g - theta div p
-// and d = w - u.  With gamma > 0 the slices follow one another in
+// u_{n+1}, Sec. III-C; the first phase then keeps g of its own tile in the
+// item's exchange buffer and the later phases load it), loads the dual field
+// p that the previous phase left in the exchange buffer (p = 0 in the first
+// phase), runs the steps with the dual field of every warp's rows in registers
+// and g in shared memory, and stores p of its own tile for the next phase,
+// or, in the last phase, u = g - theta div p and d = w - u.  With gamma > 0
+// the slices follow one another in
 // Gauss-Seidel order (one level per slice and phase); with gamma = 0 a level
 // holds one phase of every slice.  Units of a level are independent; a level
 // may start when every unit of the item's previous levels is done.  All units
@@ -65,7 +67,8 @@ struct BItem {
     const float *b;
     float *v_out;
     const uint32_t *words;
-    float *pbuf;  // [2 parities][2 components][slots][H][W], slots = 1 (gamma > 0) or Z
+    float *pbuf;  // [2 parities][2 components][slots][H][W], slots = 1 (gamma > 0) or Z;
+                  // with gamma > 0 then g [H][W] of the slice in progress
     int wstride;
     int H, W, N, R, Z;
     int hh, hc, TH, TW, tiles_x, tiles;  // row / column halo, tile rows / columns
@@ -285,9 +288,30 @@ __device__ void tv_unit(const BItem &it, const BDesc &D, int n, int j, int tile,
     const S *up = (const S *)it.u + (size_t)((n + 1) % it.Z) * HW;
 
     float2 g[RPW], gdn;
-    {
+    // with gamma > 0 and several phases, phase 0 stores g of its own tile and the
+    // later phases load it (the same FP32 values) instead of forming it again
+    const int Zp = gam > 0.f ? 1 : it.Z, slot = gam > 0.f ? 0 : n;
+    const bool gkeep = gam > 0.f && D.P > 1;
+    float *Gp = gkeep ? it.pbuf + (size_t)4 * Zp * HW : nullptr;
+    if (gkeep && j > 0) {
         float gv[2 * NR];
+        if (pairm == (1u << NR) - 1) {
 #pragma unroll
+            for (int i = 0; i < NR; ++i) {
+                const float2 v2 = __ldcg(reinterpret_cast<const float2 *>(Gp + off[i]));
+                gv[2 * i] = v2.x;
+                gv[2 * i + 1] = v2.y;
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 2 * NR; ++q)
+                gv[q] = (inm & (1u << q)) ? __ldcg(Gp + off[q >> 1] + (q & 1)) : 0.f;
+        }
+#pragma unroll
+        for (int i = 0; i < RPW; ++i) g[i] = make_float2(gv[2 * i], gv[2 * i + 1]);
+        gdn = make_float2(gv[2 * RPW], gv[2 * RPW + 1]);
+    } else {
+        float gv[2 * NR];
         if (pairm == (1u << NR) - 1) {  // every row: one load per field for both columns
 #pragma unroll
             for (int i = 0; i < NR; ++i) {
@@ -318,6 +342,13 @@ __device__ void tv_unit(const BItem &it, const BDesc &D, int n, int j, int tile,
 #pragma unroll
         for (int i = 0; i < RPW; ++i) g[i] = make_float2(gv[2 * i], gv[2 * i + 1]);
         gdn = make_float2(gv[2 * RPW], gv[2 * RPW + 1]);
+        if (gkeep) {
+#pragma unroll
+            for (int i = 0; i < RPW; ++i) {
+                if (ownm & (1u << (2 * i))) Gp[off[i]] = g[i].x;
+                if (ownm & (1u << (2 * i + 1))) Gp[off[i] + 1] = g[i].y;
+            }
+        }
     }
     // g of the warp's rows stays in shared memory over the steps (registers go
     // to the dual field); each warp reads only its own rows
@@ -326,7 +357,6 @@ __device__ void tv_unit(const BItem &it, const BDesc &D, int n, int j, int tile,
 #pragma unroll
         for (int i = 0; i < RPW; ++i) sgw[i * 32 + lane] = g[i];
     }
-    const int Zp = gam > 0.f ? 1 : it.Z, slot = gam > 0.f ? 0 : n;
     float2 p1[RPW], p2[RPW];
     float2 f1 = make_float2(0.f, 0.f), f2 = make_float2(0.f, 0.f);
 #pragma unroll
@@ -602,8 +632,9 @@ cslsm_status batch_build(const BatchSpec &spec, BatchRun &run)
         b.units_iter = b.units_x + b.units_lvl * lv;
         levels = std::max(levels, 1 + lv);
         poff[i] = pbytes;
-        if (P > 1) pbytes += (4 * (size_t)(chain ? 1 : b.Z) * s.H * s.W * sizeof(float) + 255) &
-                             ~size_t(255);
+        // p: 2 parities x 2 components x slots planes; with gamma > 0 one more plane for g
+        const size_t planes = 4 * (size_t)(chain ? 1 : b.Z) + (chain ? 1 : 0);
+        if (P > 1) pbytes += (planes * s.H * s.W * sizeof(float) + 255) & ~size_t(255);
     }
     // the units of one iteration in order: level-major, then item, then index
     std::vector<unsigned long long> tab;

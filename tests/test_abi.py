@@ -117,6 +117,10 @@ def test_newer_entry_points_reject_bad_arguments_on_host(L):
     grow = L.cslsm_unrolled_workspace_bytes(1, 4, 16, 16, ctypes.byref(kp)) - \
         L.cslsm_unrolled_workspace_bytes(1, 4, 16, 16, ctypes.byref(up))
     assert 2 * 4 * (2 * 8 + 3) * 16 * 16 * 4 <= grow <= 2 * 4 * (2 * 8 + 3) * 16 * 16 * 4 + 512
+    # batch phase length: a process-wide setting, negative values rejected
+    L.cslsm_set_batch_steps_per_phase.argtypes = [ctypes.c_int]
+    assert L.cslsm_set_batch_steps_per_phase(-1) == INVALID
+    assert L.cslsm_set_batch_steps_per_phase(0) == 0
     # the allocation-free BM3D: bad sizes and sigma, overlap
     assert L.cslsm_denoise_bm3d_noalloc(fake, ctypes.c_void_p(0x10000000), 0, 8, 8,
                                         ctypes.c_float(0.05), None) == INVALID

@@ -120,6 +120,33 @@ def test_batch_autotuned_tiles(cs):
     batch.close()
 
 
+def test_batch_forced_steps_per_phase(cs):
+    """A set phase length is used as given (clamped to T), with results equal to
+    the per-volume solves."""
+    import torch
+
+    items = _items(cs, 650)[:3]
+    prm = cs.Params(rho=1.0, lam=0.05, gamma=0.2, iters=4, denoiser="tv", tv_inner=20)
+    try:
+        cs.set_batch_steps_per_phase(3)
+        batch = cs.Batch(items, prm)
+        cs.set_batch_steps_per_phase(50)
+        batch_t = cs.Batch(items, cs.Params(rho=1.0, lam=0.05, gamma=0.2, iters=4,
+                                            denoiser="tv", tv_inner=7))
+    finally:
+        cs.set_batch_steps_per_phase(0)
+    assert batch.info()["steps_per_phase"] == 3
+    assert batch_t.info()["steps_per_phase"] == 7
+    batch_t.close()
+    batch.run()
+    batch.wait()
+    for plan, b, v in items:
+        ref = plan.solve(b, prm)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(to_np(v), to_np(ref))
+    batch.close()
+
+
 def test_batch_wait_timeout_is_reported(cs):
     items = _items(cs, 700)[:2]
     prm = cs.Params(rho=1.0, lam=0.05, gamma=0.2, iters=3, denoiser="tv", tv_inner=10)
