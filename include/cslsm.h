@@ -236,6 +236,24 @@ typedef struct {
 cslsm_status cslsm_batch_create(cslsm_batch *batch, const cslsm_batch_item *items, int n_items,
                                 const cslsm_admm_params *params, void *stream);
 
+/* Route of slice-independent TV solves (process-wide setting).  A
+ * cslsm_admm_solve with denoiser TV, lambda > 0, gamma = 0 (or Z = 1), tol = 0,
+ * init_user = 0 and no u_io / d_io gives the same bits on two paths: per-launch
+ * TV tiles (an x-update launch and a prox launch per iteration, each prox tile
+ * recomputing a halo of T + 1 pixels), or a one-item persistent batch (see
+ * cslsm_batch_create; phases of k steps with the dual field handed over through
+ * memory), which the plan creates on such a call and keeps while the
+ * parameters and the alignment class of b and v_out stay the same (other b and
+ * v_out are pointed to by a small copy on `stream`; recreating the batch
+ * synchronises the device).
+ *   mode 0 (default): the batch when one phase level holds at least 4 tiles
+ *          per SM (large volumes), else the per-launch tiles;
+ *   mode 1: always the per-launch tiles;   mode 2: always the batch.
+ * On the batch path a non-NULL stats makes the call synchronise `stream` and
+ * report a device-side wait that ran out (CSLSM_ERR_TIMEOUT).  Returns
+ * CSLSM_ERR_INVALID_ARG for other modes. */
+cslsm_status cslsm_set_tv_route(int mode);
+
 /* Chambolle steps per phase of batches created from now on (process-wide
  * setting).  k = 0 (default): the fixed default, or the timed choice under
  * cslsm_set_autotune(1).  k >= 1: exactly min(k, tv_inner, the largest phase

@@ -160,6 +160,8 @@ def lib() -> ctypes.CDLL:
     L.cslsm_set_autotune.restype = I
     L.cslsm_set_batch_steps_per_phase.argtypes = [I]
     L.cslsm_set_batch_steps_per_phase.restype = I
+    L.cslsm_set_tv_route.argtypes = [I]
+    L.cslsm_set_tv_route.restype = I
     L.cslsm_zsweep_config.argtypes = [I, I, ctypes.c_double, I]
     L.cslsm_zsweep_config.restype = I
     L.cslsm_zsweep_num_tilings.argtypes = []
@@ -327,7 +329,8 @@ def timing_enable(period: int) -> None:
 
 
 def timing_read(kernel: str, reset: bool = False) -> tuple[int, float]:
-    """(launches timed, summed device milliseconds) for one kernel name."""
+    """(launches timed, summed device milliseconds) for one kernel name; reset
+    clears the records of every kernel."""
     n = ctypes.c_longlong()
     ms = ctypes.c_double()
     _check(lib().cslsm_timing_read(kernel.encode(), ctypes.byref(n), ctypes.byref(ms),
@@ -394,6 +397,12 @@ def bm3d_stage_groups(stage: int, noisy: torch.Tensor, sigma: float,
 def set_autotune(mode: int) -> None:
     """TV tile shapes: 0 cost model, 1 timed autotuning, 2..5 force a variant."""
     _check(lib().cslsm_set_autotune(int(mode)), "cslsm_set_autotune")
+
+
+def set_tv_route(mode: int) -> None:
+    """Slice-independent TV solves: 0 auto (a one-item persistent batch for large
+    volumes), 1 per-launch tiles, 2 always the batch; the same bits either way."""
+    _check(lib().cslsm_set_tv_route(int(mode)), "cslsm_set_tv_route")
 
 
 def set_batch_steps_per_phase(k: int) -> None:

@@ -5,6 +5,7 @@
 
 #include <cmath>
 #include <cstdarg>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
@@ -50,6 +51,20 @@ struct cslsm_plan_s {
     void *bm3d_ws = nullptr;     // BM3D workspace (zero-filled on allocation)
     size_t bm3d_ws_bytes = 0;
     ZsweepWs zs;                 // persistent z sweep (TV, gamma > 0)
+    // slice-independent TV solves run as a one-item persistent batch, kept while
+    // the parameters (and the alignment class of b and v_out) stay the same
+    cslsm_batch route = nullptr;
+    struct RouteKey {
+        int io_align;  // 16, 8 or 4: alignment of the call's b and v_out
+        float rho, lambda, tau;
+        int T, iters, storage, tune, k;
+        bool operator==(const RouteKey &o) const
+        {
+            return io_align == o.io_align && rho == o.rho && lambda == o.lambda &&
+                   tau == o.tau && T == o.T && iters == o.iters && storage == o.storage &&
+                   tune == o.tune && k == o.k;
+        }
+    } route_key{};
 };
 
 namespace {
@@ -63,6 +78,9 @@ namespace {
     } while (0)
 
 inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+std::atomic<int> g_batch_k{0};   // cslsm_set_batch_steps_per_phase
+std::atomic<int> g_tv_route{0};  // cslsm_set_tv_route
 
 bool finite_f(float x) { return std::isfinite(x); }
 
@@ -114,6 +132,7 @@ Masks masks_of(const cslsm_plan_s *p) { return Masks{p->words, p->nsets > 1 ? p-
 
 void free_plan(cslsm_plan_s *p)
 {
+    if (p->route) cslsm_batch_destroy(p->route);
     cudaFree(p->words);
     cudaFree(p->u);
     cudaFree(p->d);
@@ -253,6 +272,72 @@ cslsm_status cslsm_adjoint(cslsm_plan plan, const float *b, float *v, void *stre
     return launch_adjoint(plan->g, masks_of(plan), b, v, as_stream(stream));
 }
 
+namespace {
+
+// A TV solve whose prox is slice-independent (gamma = 0 or Z = 1), with a fixed
+// iteration count from u = d = 0 in the plan's own state, can run as a one-item
+// persistent batch (the same bits as the per-launch tiles, which recompute a
+// halo of T + 1 pixels in every launch).  Auto mode takes that path when one
+// phase level holds enough tiles to fill the GPU twice over.
+bool tv_route_applies(const cslsm_plan_s *plan, const cslsm_admm_params *prm, float gam,
+                      bool use_tol, const void *u_io)
+{
+    const int mode = g_tv_route.load();
+    if (mode == 1) return false;
+    if (prm->denoiser != CSLSM_DEN_TV || !(prm->lambda > 0.f) || gam != 0.f || use_tol ||
+        prm->init_user || u_io != nullptr || prm->iters < 1)
+        return false;
+    if (mode == 2) return true;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return false;
+    const int k = std::min(prm->tv_inner, 10);
+    return (long long)plan->g.Z() * batch_tiles_per_slice(plan->g.H, plan->g.W, k) >=
+           4ll * sms;  // two CTAs per SM, twice over
+}
+
+cslsm_status batch_repoint(cslsm_batch bt, const float *b, float *v_out, cudaStream_t s);
+
+cslsm_status routed_tv_solve(cslsm_plan plan, const float *b, const cslsm_admm_params *prm,
+                             float *v_out, cslsm_admm_stats *stats, cudaStream_t s)
+{
+    const uintptr_t bv = (uintptr_t)b | (uintptr_t)v_out;
+    const int io_align = bv % 16 == 0 ? 16 : bv % 8 == 0 ? 8 : 4;
+    const cslsm_plan_s::RouteKey key{io_align,    prm->rho,     prm->lambda,
+                                     prm->tv_tau, prm->tv_inner, prm->iters,
+                                     prm->storage, tv_get_mode(), g_batch_k.load()};
+    if (plan->route && !(plan->route_key == key)) {
+        const cslsm_status st = cslsm_batch_destroy(plan->route);
+        plan->route = nullptr;
+        if (st) return st;
+    }
+    if (!plan->route) {
+        const cslsm_batch_item it{plan, b, v_out};
+        cslsm_admm_params p = *prm;
+        p.gamma = 0.f;
+        const cslsm_status st = cslsm_batch_create(&plan->route, &it, 1, &p, s);
+        if (st) {
+            plan->route = nullptr;
+            return st;
+        }
+        plan->route_key = key;
+    }
+    cslsm_status st = batch_repoint(plan->route, b, v_out, s);
+    if (st) return st;
+    st = cslsm_batch_run(plan->route, s);
+    if (st) return st;
+    if (stats) {  // reports a device-side wait that ran out (synchronises `stream`)
+        st = cslsm_batch_wait(plan->route, s);
+        if (st) return st;
+        stats->iters_done = prm->iters;
+        stats->rel_change = -1.0;
+    }
+    return CSLSM_OK;
+}
+
+}  // namespace
+
 cslsm_status cslsm_admm_solve(cslsm_plan plan, const float *b, const cslsm_admm_params *prm,
                               float *v_out, void *u_io, void *d_io, cslsm_admm_stats *stats,
                               void *stream)
@@ -275,6 +360,8 @@ cslsm_status cslsm_admm_solve(cslsm_plan plan, const float *b, const cslsm_admm_
     const size_t esz = store == CSLSM_STORE_FP32 ? 4 : 2;
     const float gam = g.Z() > 1 ? prm->gamma : 0.f;
     const bool use_tol = prm->tol > 0.f;
+    if (tv_route_applies(plan, prm, gam, use_tol, u_io))
+        return routed_tv_solve(plan, b, prm, v_out, stats, s);
     if (!prm->init_user) {
         CSLSM_CUDA(cudaMemsetAsync(u, 0, esz * nv, s));
         CSLSM_CUDA(cudaMemsetAsync(d, 0, esz * nv, s));
@@ -515,10 +602,6 @@ cslsm_status cslsm_denoise(int denoiser, const float *in, float *out, int Z, int
 
 }  // extern "C"
 
-namespace {
-std::atomic<int> g_batch_k{0};  // cslsm_set_batch_steps_per_phase
-}  // namespace
-
 struct cslsm_batch_s {
     int device;
     BatchRun run;
@@ -526,6 +609,15 @@ struct cslsm_batch_s {
     cudaGraphExec_t exec = nullptr;
     std::vector<std::pair<void *, size_t>> zero;  // state buffers zeroed by each run
 };
+
+namespace {
+
+cslsm_status batch_repoint(cslsm_batch bt, const float *b, float *v_out, cudaStream_t s)
+{
+    return batch_set_io(bt->run, 0, b, v_out, s);
+}
+
+}  // namespace
 
 namespace {
 
@@ -794,6 +886,13 @@ cslsm_status cslsm_unrolled_backward(const float *logits, const float *b, int B,
     return unrolled_backward(B, Z, H, W, p->rho, p->lambda, p->gamma, p->iters, p->tv_steps,
                              p->tv_tau, p->huber_eps, p->ckpt_every, p->keep_duals, logits, b,
                              ckpt, v_bar, logits_bar, scalar_bar, ws, as_stream(stream));
+}
+
+cslsm_status cslsm_set_tv_route(int mode)
+{
+    CHECK_ARG(mode >= 0 && mode <= 2, "TV route mode must be 0, 1 or 2");
+    g_tv_route = mode;
+    return CSLSM_OK;
 }
 
 cslsm_status cslsm_set_batch_steps_per_phase(int k)

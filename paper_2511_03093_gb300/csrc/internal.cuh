@@ -222,6 +222,9 @@ struct BatchSpec {
 // Largest number of Chambolle steps per phase whose halo fits the batched
 // solver's region.
 int batch_max_steps_per_phase();
+// TV tiles per slice of the batched solver's regions at k steps per phase (0 if
+// no tile fits).
+long long batch_tiles_per_slice(int H, int W, int k);
 
 struct BatchRun {
     void *mem = nullptr;     // one device allocation (descriptors, tables, counters)
@@ -247,6 +250,10 @@ cslsm_status unrolled_backward(int B, int Z, int H, int W, float rho, float lam,
                                cudaStream_t s);
 cslsm_status batch_build(const BatchSpec &spec, BatchRun &run);
 cslsm_status batch_set_wait(const BatchRun &run, double limit_s, int stall_test);
+// Points item `item` of a built batch at another measurement and output
+// (same alignment class as at build time), ordered on `s`.
+cslsm_status batch_set_io(const BatchRun &run, int item, const float *b, float *v_out,
+                          cudaStream_t s);
 // Enqueues the counter reset and the persistent launch (no state reset).
 cslsm_status batch_enqueue(const BatchRun &run, cudaStream_t s);
 

@@ -350,13 +350,7 @@ __device__ void tv_unit(const BItem &it, const BDesc &D, int n, int j, int tile,
             }
         }
     }
-    // g of the warp's rows stays in shared memory over the steps (registers go
-    // to the dual field); each warp reads only its own rows
     float2 *sgw = s_g + wp * RPW * 32;
-    {
-#pragma unroll
-        for (int i = 0; i < RPW; ++i) sgw[i * 32 + lane] = g[i];
-    }
     float2 p1[RPW], p2[RPW];
     float2 f1 = make_float2(0.f, 0.f), f2 = make_float2(0.f, 0.f);
 #pragma unroll
@@ -401,6 +395,11 @@ __device__ void tv_unit(const BItem &it, const BDesc &D, int n, int j, int tile,
             }
         }
     }
+    // g of the warp's rows stays in shared memory over the steps (registers go
+    // to the dual field); each warp reads only its own rows.  Stored after the p
+    // loads are issued, so that both loads are in flight together.
+#pragma unroll
+    for (int i = 0; i < RPW; ++i) sgw[i * 32 + lane] = g[i];
     if (wp == 0) {
         sb.up[0][0][lane] = f1;
         sb.up[1][0][lane] = f1;
@@ -713,6 +712,28 @@ cslsm_status batch_build(const BatchSpec &spec, BatchRun &run)
     run.k = k;
     run.units_iter = units_iter;
     return CSLSM_OK;
+}
+
+cslsm_status batch_set_io(const BatchRun &run, int item, const float *b, float *v_out,
+                          cudaStream_t s)
+{
+    // the item's measurement and output pointers in the device copy of its
+    // descriptor, ordered on `s` before the next launch (host values are staged
+    // by the copy, so the locals may go out of scope)
+    BItem *d_items = reinterpret_cast<BItem *>(run.mem);
+    const float *bp = b;
+    float *vp = v_out;
+    CSLSM_CUDA(cudaMemcpyAsync(&d_items[item].b, &bp, sizeof(bp), cudaMemcpyHostToDevice, s));
+    CSLSM_CUDA(cudaMemcpyAsync(&d_items[item].v_out, &vp, sizeof(vp), cudaMemcpyHostToDevice, s));
+    return CSLSM_OK;
+}
+
+long long batch_tiles_per_slice(int H, int W, int k)
+{
+    const int hh = k + 1, hc = hh + (hh & 1);
+    const int TH = kBRH - 2 * hh, TW = kBPW - 2 * hc;
+    if (TH < 1 || TW < 2) return 0;
+    return (long long)((W + TW - 1) / TW) * ((H + TH - 1) / TH);
 }
 
 int batch_max_steps_per_phase()

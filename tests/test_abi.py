@@ -121,6 +121,10 @@ def test_newer_entry_points_reject_bad_arguments_on_host(L):
     L.cslsm_set_batch_steps_per_phase.argtypes = [ctypes.c_int]
     assert L.cslsm_set_batch_steps_per_phase(-1) == INVALID
     assert L.cslsm_set_batch_steps_per_phase(0) == 0
+    L.cslsm_set_tv_route.argtypes = [ctypes.c_int]
+    for bad in (-1, 3):
+        assert L.cslsm_set_tv_route(bad) == INVALID
+    assert L.cslsm_set_tv_route(0) == 0
     # the allocation-free BM3D: bad sizes and sigma, overlap
     assert L.cslsm_denoise_bm3d_noalloc(fake, ctypes.c_void_p(0x10000000), 0, 8, 8,
                                         ctypes.c_float(0.05), None) == INVALID

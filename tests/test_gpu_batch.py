@@ -29,6 +29,14 @@ def cs():
 SIZES = [(8, 64, 64), (16, 96, 80), (4, 130, 101), (8, 40, 200), (1, 33, 47)]
 
 
+@pytest.fixture(autouse=True)
+def _per_launch_references(cs):
+    """Per-volume reference solves take the per-launch TV tiles, never a batch."""
+    cs.set_tv_route(1)
+    yield
+    cs.set_tv_route(0)
+
+
 def _items(cs, seed0):
     import torch
 
@@ -145,6 +153,34 @@ def test_batch_forced_steps_per_phase(cs):
         torch.cuda.synchronize()
         np.testing.assert_array_equal(to_np(v), to_np(ref))
     batch.close()
+
+
+@pytest.mark.parametrize("storage", ["fp32", "bf16"])
+def test_routed_tv_solve_equals_per_launch(cs, storage):
+    """Slice-independent TV solves routed through a one-item batch give the bits
+    of the per-launch tiles: gamma = 0, and Z = 1 with gamma > 0; a stats request
+    synchronises and reports; the kept batch is pointed at another measurement
+    buffer, and at an output that plan.solve allocates."""
+    import torch
+
+    items = _items(cs, 900)
+    for k, (plan, b, v) in enumerate(items):
+        gamma = 0.2 if plan.vol_shape[0] == 1 else 0.0
+        prm = cs.Params(rho=1.0, lam=0.05, gamma=gamma, iters=6, denoiser="tv", tv_inner=20,
+                        storage=storage)
+        cs.set_tv_route(1)
+        ref = to_np(plan.solve(b, prm))
+        cs.set_tv_route(2)
+        out = plan.solve(b, prm, v_out=v)
+        np.testing.assert_array_equal(to_np(out), ref)
+        v.zero_()
+        out, st = plan.solve(b, prm, v_out=v, stats=True)  # the kept batch, replayed
+        assert st["iters_done"] == 6
+        np.testing.assert_array_equal(to_np(out), ref)
+        b2 = b.clone()  # another buffer, the same batch
+        np.testing.assert_array_equal(to_np(plan.solve(b2, prm, v_out=v)), ref)
+        np.testing.assert_array_equal(to_np(plan.solve(b2, prm)), ref)
+        torch.cuda.synchronize()
 
 
 def test_batch_wait_timeout_is_reported(cs):
