@@ -770,6 +770,7 @@ def run_secondary(args) -> None:
         run_tvz(args)
         return
     known = ("batched_8x6", "tikhonov_1024x1024x32", "tikhonovz_1024x1024x32", "tv_1024x1024x32",
+             "tv_tiles_1024x1024x32",
              "bm3d_1024x1024x32", "tv_128x128x8", "unrolled_b8", "unrolled_b1",
              "wnnm_512x512x16", "tol_caps_512x512x16", "cr_sweep_256x256x40")
     if name not in known:
@@ -778,10 +779,14 @@ def run_secondary(args) -> None:
     clocks = start_clocks(dev)
     t_start = time.time()
     if name in ("tikhonov_1024x1024x32", "tikhonovz_1024x1024x32", "tv_1024x1024x32",
-                "bm3d_1024x1024x32", "tv_128x128x8"):
+                "tv_tiles_1024x1024x32", "bm3d_1024x1024x32", "tv_128x128x8"):
+        # tv_tiles_*: the same TV solve held on the per-launch tile kernel
+        cs.set_tv_route(1 if name.startswith("tv_tiles") else 0)
         wk = synth.WORKLOADS["tv_128x128x8" if name == "tv_128x128x8" else "bm3d_1024x1024x32"]
         data = synth.generate(wk)
         den = name.split("_")[0]
+        if name.startswith("tv_tiles"):
+            out["path"] = "per-launch TV tiles (cslsm_set_tv_route(1))"
         gam = 0.2 if den == "tikhonovz" else 0.0  # Tikhonov with the z term (Sec. III-C)
         den = "tikhonov" if den == "tikhonovz" else den
         iters = 50 if name == "tv_128x128x8" else 30
@@ -993,7 +998,8 @@ def main():
     ap.add_argument("--workload", default=None,
                     help="secondary workload: tvz_512x512x16, batched_8x6, tikhonov_1024x1024x32, "
                          "tikhonovz_1024x1024x32, "
-                         "tv_1024x1024x32, bm3d_1024x1024x32, tv_128x128x8, unrolled_b8, unrolled_b1, "
+                         "tv_1024x1024x32, tv_tiles_1024x1024x32, bm3d_1024x1024x32, tv_128x128x8, "
+                         "unrolled_b8, unrolled_b1, "
                          "cr_sweep_256x256x40, tol_caps_512x512x16, wnnm_512x512x16")
     args = ap.parse_args()
     if args.workload:
