@@ -46,7 +46,7 @@ METRIC = "PnP-ADMM voxel-iterations/s"
 UNIT = "voxel-it/s"
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 DOMINANT = "batch_persistent"  # one launch = the whole 60-iteration batch
-BATCH_PROFILE_K = 5  # steps per phase of the 8-item profiling case (see batched_8x6)
+BATCH_PROFILE_K = 7  # steps per phase of the 8-item profiling case (see batched_8x6)
 DOMINANT_SOURCES = ("kernels_batch.cu", "tv_body.cuh", "storage.cuh")
 TVZ_DOMINANT = "tvz_sweep"  # the single-volume configuration's dominant kernel
 TVZ_SOURCES = ("kernels_tvz.cu", "tv_body.cuh", "storage.cuh")

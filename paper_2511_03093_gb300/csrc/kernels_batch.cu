@@ -24,10 +24,11 @@
 // single-volume sweep.
 //
 // Scheduling.  The grid is exactly as many CTAs as fit on the GPU at once
-// (two 256-thread CTAs per SM, so that one CTA's loads and barriers overlap
-// the other's Chambolle steps).  Each CTA holds a current unit number and
-// reserves the next one from a global ticket counter while it works (the
-// atomic's latency hides behind the unit); a unit number is decoded by one
+// (three 256-thread CTAs per SM at 80 registers a thread, so that one CTA's
+// loads and barriers overlap the others' Chambolle steps; measured faster than
+// two CTAs at 128 registers despite the spills).  Each CTA holds a current
+// unit number and reserves the next one from a global ticket counter while it
+// works (the atomic's latency hides behind the unit); a unit number is decoded by one
 // lookup in a per-iteration table of (item, level, index).  Before it starts
 // a unit the CTA waits until the item's completed-unit counter (read with
 // acquire semantics) reaches the count the unit depends on; it increments the
@@ -55,8 +56,8 @@
 namespace cslsm {
 namespace {
 
-constexpr int kBW = 8, kBR = 12;     // warps per CTA, rows of the region per warp
-constexpr int kBNT = kBW * 32;       // 256 threads per CTA, two CTAs per SM
+constexpr int kBW = 8, kBR = 11;     // warps per CTA, rows of the region per warp
+constexpr int kBNT = kBW * 32;       // 256 threads per CTA, three CTAs per SM
 constexpr int kBRH = kBW * kBR + 2;  // region rows
 // a warp's row masks hold 2 bits (columns) for each of its kBR + 1 rows
 static_assert(2 * (kBR + 1) <= 32, "row masks are 32-bit");
@@ -421,10 +422,10 @@ __device__ void tv_unit(const BItem &it, const BDesc &D, int n, int j, int tile,
     const int lo = hh - (j == D.P - 1 ? 1 : 0), hi = hh + TH;
     const float2 *sgr = sgw;
     if (interior)
-        sweep_steps<true, B, RPW>(sb, p1, p2, sgr, gdn, mr, mc0, mc1, inv_theta, D.tau, ns, wp,
+        sweep_steps<true, B, RPW, true>(sb, p1, p2, sgr, gdn, mr, mc0, mc1, inv_theta, D.tau, ns, wp,
                                   lane, lo, hi);
     else
-        sweep_steps<false, B, RPW>(sb, p1, p2, sgr, gdn, mr, mc0, mc1, inv_theta, D.tau, ns, wp,
+        sweep_steps<false, B, RPW, true>(sb, p1, p2, sgr, gdn, mr, mc0, mc1, inv_theta, D.tau, ns, wp,
                                    lane, lo, hi);
     // Every row pairs up (pairm full) only when W is even, so every plane and
     // buffer offset is even and a lane's two columns take one aligned access.
@@ -488,7 +489,7 @@ __device__ void tv_unit(const BItem &it, const BDesc &D, int n, int j, int tile,
 }
 
 template <typename S>
-__global__ void __launch_bounds__(kBNT, 2) batch_persistent_kernel(const BDesc *__restrict__ dp)
+__global__ void __launch_bounds__(kBNT, 3) batch_persistent_kernel(const BDesc *__restrict__ dp)
 {
     __shared__ Bnd<kBW> sb;
     __shared__ float2 s_g[kBW * kBR * 32];  // g of each warp's rows during a TV unit

@@ -175,8 +175,12 @@ __device__ __forceinline__ float2 g_row(const G &g, int i, int lane)
 // read only by rows outside the band of the next step, so the rows that
 // matter get exactly the values of a full update.
 //
-// g (constant over the steps) is read through g_row.
-template <bool INTERIOR, int B, int RPW, typename G>
+// g (constant over the steps) is read through g_row.  ROLL: q of row i + 1 is
+// formed just before row i's update instead of q of every row first, so two q
+// values are live instead of RPW + 1 (the shuffles keep their order, so the
+// compiler cannot interleave the other way round); the same operations on the
+// same values, so the same bits.
+template <bool INTERIOR, int B, int RPW, bool ROLL = false, typename G>
 __device__ __forceinline__ void sweep_steps(Bnd<B> &sb, float2 (&p1)[RPW], float2 (&p2)[RPW],
                                             const G &g, float2 gdn,
                                             const float (&mr)[RPW], float mc0, float mc1,
@@ -191,6 +195,30 @@ __device__ __forceinline__ void sweep_steps(Bnd<B> &sb, float2 (&p1)[RPW], float
         if (r0 + RPW > lo - e && r0 < hi + e) {
             const float2 pu0 = sb.up[par][wp][lane];
             const float2 dn1 = sb.dn1[par][wp][lane], dn2 = sb.dn2[par][wp][lane];
+            if (ROLL) {
+                // row by row: q of row i + 1 (from the old p1 of row i), then row
+                // i's update; two q values live instead of RPW + 1
+                float2 qc = q_pair(p1[0], pu0, p2[0], __shfl_up_sync(FULL, p2[0].y, 1),
+                                   g_row(g, 0, lane), inv_theta);
+#pragma unroll
+                for (int i = 0; i < RPW; ++i) {
+                    const float2 qn =
+                        i + 1 < RPW
+                            ? q_pair(p1[i + 1], p1[i], p2[i + 1],
+                                     __shfl_up_sync(FULL, p2[i + 1].y, 1),
+                                     g_row(g, i + 1, lane), inv_theta)
+                            : q_pair(dn1, p1[RPW - 1], dn2, __shfl_up_sync(FULL, dn2.y, 1), gdn,
+                                     inv_theta);
+                    const float qr = __shfl_down_sync(FULL, qc.x, 1);
+                    float2 p2n = p2[i];
+                    const float2 p1n =
+                        INTERIOR ? chambolle_pair_interior(qc, qn, qr, p1[i], tau, p2n)
+                                 : chambolle_pair(qc, qn, qr, p1[i], mr[i], mc0, mc1, tau, p2n);
+                    p1[i] = p1n;
+                    p2[i] = p2n;
+                    qc = qn;
+                }
+            } else {
             float2 q[RPW + 1];
 #pragma unroll
             for (int i = 0; i < RPW; ++i)
@@ -207,6 +235,7 @@ __device__ __forceinline__ void sweep_steps(Bnd<B> &sb, float2 (&p1)[RPW], float
                                               p2n);
                 p1[i] = p1n;
                 p2[i] = p2n;
+            }
             }
             if (wp + 1 < B) sb.up[nxt][wp + 1][lane] = p1[RPW - 1];
             if (wp > 0) {
