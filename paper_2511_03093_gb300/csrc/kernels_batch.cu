@@ -263,7 +263,7 @@ __device__ void tv_unit(const BItem &it, const BDesc &D, int n, int j, int tile,
                           inc[1] && j0 + 1 >= hc && j0 + 1 < hc + TW};
     const bool interior = gi0 >= 0 && gi0 + RH < H && gj0 >= 0 && gj0 + kBPW < W;
     const unsigned Hm1 = (unsigned)(H - 1);
-    float mr[RPW];
+    unsigned mr = 0;  // bit i: row i has a row below it in the image
     int off[NR];
     unsigned inm = 0, ownm = 0, pairm = 0;  // pairm: both columns in, pair aligned
 #pragma unroll
@@ -278,7 +278,7 @@ __device__ void tv_unit(const BItem &it, const BDesc &D, int n, int j, int tile,
             if (i < RPW && inr && ownc[c] && r0 + i >= hh && r0 + i < hh + TH)
                 ownm |= 1u << (2 * i + c);
         }
-        if (i < RPW) mr[i] = (unsigned)gi < Hm1 ? 1.f : 0.f;
+        if (i < RPW && (unsigned)gi < Hm1) mr |= 1u << i;
     }
     const float gam = it.Z > 1 ? D.gam : 0.f;
     const float rho = D.rho, inv_rho2g = 1.f / (D.rho + 2.f * gam);

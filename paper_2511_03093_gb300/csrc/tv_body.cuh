@@ -154,6 +154,13 @@ struct Bnd {
 // Row i of g for a lane: from a register array of the warp's rows, or from the
 // warp's rows in shared memory ([RPW][32] float2), which frees 2 RPW registers
 // for taller regions at one shared load per row and step.
+// Row mask of row i (1 where the row has a row below it in the image): from an
+// array of the warp's rows, or from bit i of a word (fewer registers).
+template <int RPW>
+__device__ __forceinline__ float mr_at(const float (&mr)[RPW], int i) { return mr[i]; }
+template <int RPW>
+__device__ __forceinline__ float mr_at(unsigned mr, int i) { return (mr >> i) & 1u ? 1.f : 0.f; }
+
 template <typename G>
 __device__ __forceinline__ float2 g_row(const G &g, int i, int lane)
 {
@@ -180,10 +187,10 @@ __device__ __forceinline__ float2 g_row(const G &g, int i, int lane)
 // values are live instead of RPW + 1 (the shuffles keep their order, so the
 // compiler cannot interleave the other way round); the same operations on the
 // same values, so the same bits.
-template <bool INTERIOR, int B, int RPW, bool ROLL = false, typename G>
+template <bool INTERIOR, int B, int RPW, bool ROLL = false, typename G, typename MR>
 __device__ __forceinline__ void sweep_steps(Bnd<B> &sb, float2 (&p1)[RPW], float2 (&p2)[RPW],
                                             const G &g, float2 gdn,
-                                            const float (&mr)[RPW], float mc0, float mc1,
+                                            const MR &mr, float mc0, float mc1,
                                             float inv_theta, float tau, int ns, int wp, int lane,
                                             int lo, int hi)
 {
@@ -213,7 +220,7 @@ __device__ __forceinline__ void sweep_steps(Bnd<B> &sb, float2 (&p1)[RPW], float
                     float2 p2n = p2[i];
                     const float2 p1n =
                         INTERIOR ? chambolle_pair_interior(qc, qn, qr, p1[i], tau, p2n)
-                                 : chambolle_pair(qc, qn, qr, p1[i], mr[i], mc0, mc1, tau, p2n);
+                                 : chambolle_pair(qc, qn, qr, p1[i], mr_at<RPW>(mr, i), mc0, mc1, tau, p2n);
                     p1[i] = p1n;
                     p2[i] = p2n;
                     qc = qn;
@@ -231,7 +238,7 @@ __device__ __forceinline__ void sweep_steps(Bnd<B> &sb, float2 (&p1)[RPW], float
                 float2 p2n = p2[i];
                 const float2 p1n =
                     INTERIOR ? chambolle_pair_interior(q[i], q[i + 1], qr, p1[i], tau, p2n)
-                             : chambolle_pair(q[i], q[i + 1], qr, p1[i], mr[i], mc0, mc1, tau,
+                             : chambolle_pair(q[i], q[i + 1], qr, p1[i], mr_at<RPW>(mr, i), mc0, mc1, tau,
                                               p2n);
                 p1[i] = p1n;
                 p2[i] = p2n;
