@@ -183,6 +183,35 @@ def test_routed_tv_solve_equals_per_launch(cs, storage):
         torch.cuda.synchronize()
 
 
+@pytest.mark.parametrize("per_slice", [True, False])
+def test_routed_tv_solve_multishot(cs, per_slice):
+    """Several coded shots of R planes (patterns per slice, or shared by every
+    shot): the routed solve and a batch of the item give the bits of the
+    per-launch tiles."""
+    import torch
+
+    Z, H, W, N = 12, 72, 88, 3
+    R = Z // N
+    wk = synth.Workload("ms", Z, H, W, n_shots=N, per_slice_masks=per_slice, drift=True,
+                        mask_p=0.5, peak=200.0, sigma_g=0.01, seed=1400 + int(per_slice),
+                        n_blobs=40)
+    data = synth.generate(wk)
+    plan = cs.Plan(H, W, N, R, to_dev(data["masks"]), per_slice=per_slice)
+    b = to_dev(data["b"])
+    prm = cs.Params(rho=1.0, lam=0.05, gamma=0.0, iters=5, denoiser="tv", tv_inner=20)
+    cs.set_tv_route(1)
+    ref = to_np(plan.solve(b, prm))
+    cs.set_tv_route(2)
+    np.testing.assert_array_equal(to_np(plan.solve(b, prm)), ref)
+    v = torch.empty(plan.vol_shape, dtype=torch.float32, device="cuda")
+    batch = cs.Batch([(plan, b, v)], prm)
+    batch.run()
+    batch.wait()
+    np.testing.assert_array_equal(to_np(v), ref)
+    batch.close()
+    plan.close()
+
+
 def test_batch_wait_timeout_is_reported(cs):
     items = _items(cs, 700)[:2]
     prm = cs.Params(rho=1.0, lam=0.05, gamma=0.2, iters=3, denoiser="tv", tv_inner=10)
