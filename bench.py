@@ -508,6 +508,16 @@ def run_ours(args) -> None:
                     "share_of_step": ms_dom / total_ms}
             if tr:
                 roof["traffic_per_voxel_it_B"] = tr / (vox * PARAMS["iters"])
+                roof["traffic_GBs"] = tr / avg_s / 1e9
+            # the same launch against the FP32 ALU: the algorithmic operations of the
+            # x-update-free TV + z prox (19 per pixel and step + 11 per pixel), the
+            # view for a kernel whose data stays on chip
+            fl = PARAMS["iters"] * sum(w.Z * tv_flops_per_launch(w.H, w.W, PARAMS["tv_inner"])
+                                       for w in ws)
+            alu_peak = alu_peak_tflops((clk or {}).get("sm_max_mhz") or 2070.0)
+            roof["alu_view"] = {"achieved": fl / avg_s / 1e12, "peak": alu_peak,
+                                "unit": "TFLOP/s", "frac": fl / avg_s / 1e12 / alu_peak,
+                                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"}
         # the comparison the metric names: plain per-volume FP32 solves of the same
         # items, and the batch with FP32 state, each run once (not in the timed region)
         x_d = [torch.from_numpy(d["x"]).to(dev) for d in datas]
