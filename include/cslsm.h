@@ -247,7 +247,8 @@ cslsm_status cslsm_batch_create(cslsm_batch *batch, const cslsm_batch_item *item
  * v_out are pointed to by a small copy on `stream`; recreating the batch
  * synchronises the device).
  *   mode 0 (default): the batch when one phase level holds at least 4 tiles
- *          per SM (large volumes), else the per-launch tiles;
+ *          per SM (large volumes), else the per-launch tiles; a batch that does
+ *          not fit in device memory leaves the solve to the per-launch tiles;
  *   mode 1: always the per-launch tiles;   mode 2: always the batch.
  * On the batch path a non-NULL stats makes the call synchronise `stream` and
  * report a device-side wait that ran out (CSLSM_ERR_TIMEOUT).  Returns

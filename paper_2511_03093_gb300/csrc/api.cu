@@ -360,8 +360,13 @@ cslsm_status cslsm_admm_solve(cslsm_plan plan, const float *b, const cslsm_admm_
     const size_t esz = store == CSLSM_STORE_FP32 ? 4 : 2;
     const float gam = g.Z() > 1 ? prm->gamma : 0.f;
     const bool use_tol = prm->tol > 0.f;
-    if (tv_route_applies(plan, prm, gam, use_tol, u_io))
-        return routed_tv_solve(plan, b, prm, v_out, stats, s);
+    if (tv_route_applies(plan, prm, gam, use_tol, u_io)) {
+        st = routed_tv_solve(plan, b, prm, v_out, stats, s);
+        // auto mode: a batch that does not fit (memory) leaves the solve to the
+        // per-launch tiles; a forced batch reports it
+        if (st != CSLSM_ERR_OOM || g_tv_route.load() == 2) return st;
+        cudaGetLastError();  // the failed allocation's (non-sticky) error
+    }
     if (!prm->init_user) {
         CSLSM_CUDA(cudaMemsetAsync(u, 0, esz * nv, s));
         CSLSM_CUDA(cudaMemsetAsync(d, 0, esz * nv, s));
