@@ -27,8 +27,10 @@
 // iterates and runs their adjoint), the x-update.  Gradients: dL/dlogits and
 // the three scalars dL/drho, dL/dlambda, dL/dgamma (FP64 accumulators).
 //
-// Kernels are plain one-thread-per-pixel passes (a block row of the grid per
-// batch item); the stencils read their neighbours from global memory (L1/L2).
+// Kernels are one-thread-per-pixel passes (a block row of the grid per batch
+// item); the stencils read their neighbours from global memory (L1/L2), except
+// that the forward dual step forms q once per tile in shared memory and the
+// reverse dual step works on shared-memory tiles.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -209,38 +211,42 @@ struct DualArgs {
     float inv_theta, tau, kappa;
 };
 
-// a = p + tau (grad q - kappa p) at pixel (i, j) of item bi; returns a1, a2.
-__device__ __forceinline__ void dual_a(const float *p1, const float *p2, const float *h, int i,
-                                       int j, int H, int W, float inv_theta, float tau, float kappa,
-                                       float &a1, float &a2)
-{
-    const float qc = qval(p1, p2, h, i, j, H, W, inv_theta);
-    const float gx = i < H - 1 ? qval(p1, p2, h, i + 1, j, H, W, inv_theta) - qc : 0.f;
-    const float gy = j < W - 1 ? qval(p1, p2, h, i, j + 1, H, W, inv_theta) - qc : 0.f;
-    const size_t o = (size_t)i * W + j;
-    a1 = p1[o] + tau * (gx - kappa * p1[o]);
-    a2 = p2[o] + tau * (gy - kappa * p2[o]);
-}
-
-// One thread per pixel on a 2-D grid: blocks of 32 columns x 8 rows (rows
-// grid-strided), z = batch item.
+// One step p <- proj(p + tau (grad q - kappa p)) on a 2-D grid: blocks of 32
+// columns x 8 rows (row chunks grid-strided), z = batch item.  q is formed once
+// per pixel of the chunk, plus the row below and the column to the right that
+// grad q reads, into shared memory (by qval, as everywhere, so the same bits),
+// instead of three times per pixel.
 __global__ void __launch_bounds__(kT) dual_fwd_kernel(const DualArgs A)
 {
+    constexpr int R = kT / 32;  // rows per chunk
+    __shared__ float s_q[R + 1][33];
     const Geo &g = A.g;
-    const int j = (int)blockIdx.x * 32 + (int)(threadIdx.x & 31);
+    const int lane = (int)(threadIdx.x & 31), wr = (int)(threadIdx.x >> 5);
+    const int j0 = (int)blockIdx.x * 32, j = j0 + lane;
     const int bi = blockIdx.z;
-    if (j >= g.W) return;
     const float *p1 = A.P + (size_t)bi * 2 * g.HW(), *p2 = p1 + g.HW();
     const float *h = A.Hb + (size_t)bi * g.HW();
     float *n1 = A.Pn + (size_t)bi * 2 * g.HW(), *n2 = n1 + g.HW();
-    for (int i = (int)blockIdx.y * (kT / 32) + (int)(threadIdx.x >> 5); i < g.H;
-         i += (int)gridDim.y * (kT / 32)) {
-        const int p = i * g.W + j;  // H W < 2^31
-        float a1, a2;
-        dual_a(p1, p2, h, i, j, g.H, g.W, A.inv_theta, A.tau, A.kappa, a1, a2);
-        const float sc = 1.f / fmaxf(1.f, sqrtf(a1 * a1 + a2 * a2));
-        n1[p] = a1 * sc;
-        n2[p] = a2 * sc;
+    for (int i0 = (int)blockIdx.y * R; i0 < g.H; i0 += (int)gridDim.y * R) {
+        for (int t = (int)threadIdx.x; t < (R + 1) * 33; t += kT) {
+            const int r = t / 33, c = t - r * 33;
+            const int qi = i0 + r, qj = j0 + c;
+            if (qi < g.H && qj < g.W) s_q[r][c] = qval(p1, p2, h, qi, qj, g.H, g.W, A.inv_theta);
+        }
+        __syncthreads();
+        const int i = i0 + wr;
+        if (i < g.H && j < g.W) {
+            const float qc = s_q[wr][lane];
+            const float gx = i < g.H - 1 ? s_q[wr + 1][lane] - qc : 0.f;
+            const float gy = j < g.W - 1 ? s_q[wr][lane + 1] - qc : 0.f;
+            const size_t o = (size_t)i * g.W + j;
+            const float a1 = p1[o] + A.tau * (gx - A.kappa * p1[o]);
+            const float a2 = p2[o] + A.tau * (gy - A.kappa * p2[o]);
+            const float sc = 1.f / fmaxf(1.f, sqrtf(a1 * a1 + a2 * a2));
+            n1[o] = a1 * sc;
+            n2[o] = a2 * sc;
+        }
+        __syncthreads();
     }
 }
 
