@@ -1,5 +1,5 @@
-"""Host-side logic of bench.py that needs no GPU: the clock-sample summary and the
-streaming byte model of the TV path."""
+"""Host-side logic of bench.py that needs no GPU: the clock-sample summary, the
+streaming byte model of the TV path and the committed profile records."""
 import datetime
 import time
 
@@ -53,3 +53,29 @@ def test_oracle_sample_is_stratified_by_size():
         assert sizes[8 * k] <= v <= sizes[8 * k + 7]
     # replicas draw different batches
     assert [w.seed for w in bench.rank_workloads(1)] != [w.seed for w in ws]
+
+
+def test_profile_records_follow_the_kernel_sources(tmp_path, monkeypatch):
+    """A committed ncu record counts only while the kernel's sources hash as when
+    it was taken; the L2 view divides its bytes by the launch time of the run."""
+    import json
+
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    rec = {"sources_sha256_16": bench._kernel_hash(bench.TVZ_SOURCES),
+           "dram_bytes_per_launch": 1.0e6, "l2_bytes_per_launch": 4.0e9, "l2_peak_GBs": 40000.0,
+           "l2_sector_hit_rate_pct": 70.0}
+    (prof / "k_w.json").write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    # the source hash still reads the package sources
+    monkeypatch.setattr(bench, "_kernel_hash",
+                        lambda sources: rec["sources_sha256_16"] if sources == bench.TVZ_SOURCES
+                        else "0" * 16)
+    assert bench._traffic("k", "w", bench.TVZ_SOURCES) == 1.0e6
+    l2 = bench._l2("k", "w", bench.TVZ_SOURCES, 1e-3)
+    assert l2["achieved"] == 4.0e9 / 1e-3 / 1e9 and l2["frac"] == l2["achieved"] / 40000.0
+    assert l2["unit"] == "GB/s"
+    # another kernel source: the record no longer applies
+    assert bench._traffic("k", "w", bench.DOMINANT_SOURCES) is None
+    assert bench._l2("k", "w", bench.DOMINANT_SOURCES, 1e-3) is None
+    assert bench._record("missing", "w", bench.TVZ_SOURCES) == {}
